@@ -1,0 +1,165 @@
+/*
+ * aceapex.h -- C ABI of the GB300 ACEAPEX stream decoder (libaceapex.so).
+ *
+ * ACEAPEX is an LZ77 format whose back-references are absolute positions in the decoded output and whose
+ * output is cut into self-contained blocks of B bytes (paper §3.1); each block carries four arrays:
+ * literal bytes, match lengths, absolute offsets and the command sequence of literal-run lengths (§3.2).
+ * The byte layout is fixed in FORMAT.md.  Decoding places every sequence with a prefix sum, scatters the
+ * literals and runs the match copies in dependency-depth waves (§7.1); a stream whose matches all read
+ * literal bytes (chain flattening, §3.3) decodes in one pass.
+ *
+ * Conventions for every call:
+ *   - pointers named d_* and the comp/out arguments of the decode calls are DEVICE pointers owned by the
+ *     caller; the library never frees them;
+ *   - `stream` is a cudaStream_t (passed as void*); work is enqueued on it in order;
+ *   - return values are aceapex_status codes (0 = OK, negative = error); no C++ exception crosses the ABI;
+ *   - malformed input never faults the GPU: every device load and store is bounds-checked and a violation
+ *     becomes a status code;
+ *   - calls on one context are serialised by an internal lock; use one stream per concurrent decode.
+ */
+#ifndef ACEAPEX_H
+#define ACEAPEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ACEAPEX_OK = 0,
+    ACEAPEX_ERR_ARG = -1,     /* null pointer, misaligned comp (needs 16 B), bad size argument */
+    ACEAPEX_ERR_FORMAT = -2,  /* bad magic/version/flags/fields, block index, header counts, varint, sync table */
+    ACEAPEX_ERR_SIZE = -3,    /* out_len differs from the decoded size, comp_len differs from the header */
+    ACEAPEX_ERR_OFFSET = -4,  /* a match source not before its destination, or a sequence leaving its block */
+    ACEAPEX_ERR_TIMEOUT = -5, /* a bounded device wait expired (the result is unusable, the context is fine) */
+    ACEAPEX_ERR_CUDA = -6,    /* a CUDA runtime call failed */
+    ACEAPEX_ERR_NOMEM = -7,   /* workspace allocation failed, or the caller's workspace is too small */
+    ACEAPEX_ERR_DEPTH = -8    /* the stream's max_depth is smaller than the depth of one of its matches */
+} aceapex_status;
+
+/* Header fields of a stream (FORMAT.md §1.1). */
+typedef struct {
+    uint64_t decoded_len;   /* N */
+    uint64_t n_blocks;      /* ceil(N / B) */
+    uint64_t comp_len;      /* total stream bytes */
+    uint64_t n_match;       /* matches over all blocks */
+    uint64_t n_seq;         /* sequences over all blocks */
+    uint64_t n_tiles;       /* sync-point tiles over all blocks */
+    uint32_t block_log2;    /* B = 2^block_log2 */
+    uint32_t tile_log2;     /* T = 2^tile_log2 */
+    uint32_t min_match;
+    uint32_t flatten;       /* 0 none, 1 within-block, 2 global (§3.3) */
+    uint32_t depth_cap;     /* 0 = none (§7.4) */
+    uint32_t max_depth;     /* largest match depth; <= 1 selects the one-pass decode */
+} aceapex_info;
+
+/* Statistics of the last decode on this context (aceapex_get_stats). */
+#define ACEAPEX_HIST_MAX 4096
+typedef struct {
+    uint64_t decoded_len, comp_len, n_match, n_tiles;
+    uint32_t max_depth;         /* largest match depth of the stream */
+    uint32_t one_pass;          /* 1 when the one-pass (flattened) path ran */
+    uint32_t n_levels;          /* depth levels executed by the wavefront (0 on the one-pass path) */
+    uint32_t hist_len;          /* valid entries of level_hist */
+    uint64_t level_hist[ACEAPEX_HIST_MAX]; /* level_hist[k] = matches of depth k (k >= 1), clipped */
+} aceapex_stats;
+
+/* Host-side header parse.  host_prefix holds at least the first 64 bytes of the stream.
+ * Checks magic, version, flags and field ranges (FORMAT.md §1.1). */
+int aceapex_peek_header(const void *host_prefix, size_t len, aceapex_info *info);
+
+/* Device workspace bytes needed by aceapex_decode_async for this stream. */
+size_t aceapex_workspace_size(const aceapex_info *info);
+
+/*
+ * Decode one stream (blocking).  comp: device bytes of the stream, 16-byte aligned, comp_len bytes.
+ * out: device buffer of out_len bytes, which must equal the header's decoded length.  Reads the 64-byte
+ * header back to the host, takes workspace from a cached pool, enqueues the decode on `stream`,
+ * synchronises `stream` and returns the device status.
+ */
+int aceapex_decode(const void *comp, size_t comp_len, void *out, size_t out_len, void *stream);
+
+/*
+ * Decode one stream without any host synchronisation.  info: from aceapex_peek_header on a host copy of
+ * the header.  d_ws: caller-owned device workspace of at least aceapex_workspace_size(info) bytes,
+ * zero-filled before its first use (it may then be reused without clearing by calls that do not
+ * overlap in time).  d_status: device int32 that receives the status.  Returns an argument error at
+ * once; device-side errors go to *d_status.
+ */
+int aceapex_decode_async(const void *comp, size_t comp_len, void *out, size_t out_len, const aceapex_info *info,
+                         void *d_ws, size_t ws_len, int32_t *d_status, void *stream);
+
+/*
+ * Decode n independent streams (blocking).  comps/outs: host arrays of n device pointers; comp_lens and
+ * out_lens: host arrays; statuses: host array of n int32 that receives each stream's status.  Streams
+ * whose matches all have depth <= 1 are decoded together by one persistent launch over a global tile
+ * queue; the others are decoded one after another.  Returns 0 when every stream decoded, else the first
+ * failing status.
+ */
+int aceapex_decode_batch(int n, const void *const *comps, const size_t *comp_lens, void *const *outs,
+                         const size_t *out_lens, int32_t *statuses, void *stream);
+
+/*
+ * Reusable batch plan (for repeated decodes of the same set of buffers): reads the headers once, builds the
+ * device descriptor table and workspace.  plan_launch enqueues the decode; with graph != 0 the launch
+ * sequence is captured into a CUDA graph on first use and replayed afterwards.  plan_statuses copies the
+ * per-stream statuses to the host (synchronising `stream`).
+ */
+typedef struct aceapex_batch_plan aceapex_batch_plan;
+int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *comp_lens, void *const *outs,
+                              const size_t *out_lens, void *stream, aceapex_batch_plan **plan);
+int aceapex_batch_plan_launch(aceapex_batch_plan *plan, int graph, void *stream);
+int aceapex_batch_plan_statuses(aceapex_batch_plan *plan, int32_t *statuses, void *stream);
+int aceapex_batch_plan_destroy(aceapex_batch_plan *plan);
+
+/* Launch shape of the one-pass kernel: threads per CTA (128, 256 or 512), CTAs per SM (0 = as many as
+ * fit), sequences per thread per parse chunk (2, 4 or 8).  Applies to later launches on this context. */
+int aceapex_set_launch_config(int threads, int ctas_per_sm, int seqs_per_thread);
+int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *seqs_per_thread);
+
+/* Decode every stream with the wavefront path, even streams whose max_depth <= 1 would take the one-pass
+ * kernel (for testing and comparison).  Applies to later calls on this context. */
+int aceapex_set_force_wavefront(int on);
+
+/* Limit of every bounded device wait in nanoseconds (0 restores the default of 4 s).  withhold_tile is a
+ * test hook: the one-pass kernel's tile with that global index never publishes its literals, so that
+ * every later tile's wait runs out and the call returns ACEAPEX_ERR_TIMEOUT without faulting the GPU
+ * (UINT64_MAX = none).  Applies to later launches on this context. */
+int aceapex_set_wait_limit(uint64_t ns, uint64_t withhold_tile);
+
+/* Kernel timing.  aceapex_profile(1) clears the totals and starts recording a CUDA event pair on the launch
+ * stream around every kernel the library launches (not inside CUDA-graph capture); aceapex_profile(0)
+ * stops.  aceapex_profile_read synchronises on the recorded events, adds them to the per-kernel totals
+ * and fills up to max_kernels entries (kernel name, total milliseconds, launch count); it returns the
+ * number of kernels the library has. */
+int aceapex_profile(int enable);
+int aceapex_profile_read(int max_kernels, const char **names, double *total_ms, uint64_t *launches);
+
+/* Statistics of the last aceapex_decode on this context (level histogram only when the wavefront ran). */
+int aceapex_get_stats(aceapex_stats *stats);
+
+/* Human-readable name of a status code. */
+const char *aceapex_strerror(int code);
+
+/* ------------------------------------------------------------------------------------------- encoder */
+/* Encoder parameters (host side, CPU).  Defaults: block_log2 20, tile_log2 14, min_match 4,
+ * hash_bits 20, chain_limit 16, flatten 0, depth_cap 0, use_first 1, min_emit 0. */
+typedef struct {
+    uint32_t block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit;
+} aceapex_enc_params;
+
+/*
+ * Encode n host bytes into a newly allocated host buffer (*out, release with aceapex_free).  Greedy
+ * hash-chain parse with absolute offsets (§3.1, §3.4), optional chain flattening (§3.3) and depth cap
+ * (§7.4).  Returns the stream length or a negative status.  Inputs must be shorter than 4 GiB;
+ * chain_limit <= 16, 8 <= hash_bits <= 24.
+ */
+int64_t aceapex_encode(const void *in, size_t n, const aceapex_enc_params *params, void **out);
+void aceapex_free(void *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACEAPEX_H */

@@ -1,0 +1,325 @@
+"""GB300 ACEAPEX stream decoder: Python binding of libaceapex.so (C ABI in include/aceapex.h).
+
+Argument marshalling only: every step of the decode runs in the library's CUDA kernels, and the encoder
+in its C++ code.  PyTorch supplies device memory and streams.  Importing this module never falls back to
+anything: if the shared library is missing, calls raise.
+
+    import paper_2606_04268_gb300 as ax
+    comp = ax.encode(data_bytes, flatten=2)            # numpy uint8 stream (CPU encoder)
+    d_comp = torch.from_numpy(comp).cuda()
+    d_out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ax.decode(d_comp, d_out)                           # raises AceapexError on a bad stream
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+LIB_PATH = os.path.join(_HERE, "libaceapex.so")
+_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp"]
+_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh"]
+NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+OK, ERR_ARG, ERR_FORMAT, ERR_SIZE, ERR_OFFSET, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_DEPTH = 0, -1, -2, -3, -4, -5, -6, -7, -8
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_FORMAT", -3: "ERR_SIZE", -4: "ERR_OFFSET", -5: "ERR_TIMEOUT",
+                -6: "ERR_CUDA", -7: "ERR_NOMEM", -8: "ERR_DEPTH"}
+FLAT_NONE, FLAT_BLOCK, FLAT_GLOBAL = 0, 1, 2
+HIST_MAX = 4096
+
+
+class AceapexError(RuntimeError):
+    def __init__(self, code: int, what: str = "aceapex"):
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+# ---------------------------------------------------------------------------------------------- build
+def _nvcc() -> str:
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = [os.path.join(_CSRC, f) for f in _SOURCES + _HEADERS] + [os.path.join(_INCLUDE, "aceapex.h")]
+    return any(os.path.getmtime(p) > t for p in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libaceapex.so for sm_103a in-tree (nvcc, one -gencode, translation units in parallel)."""
+    if not force and not _stale():
+        return LIB_PATH
+    nvcc = _nvcc()
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    objdir = os.path.join(_HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    common = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", f"-I{_INCLUDE}"] + NVCC_ARCH
+
+    def compile_one(src: str) -> str:
+        obj = os.path.join(objdir, src + f".{os.getpid()}.o")
+        cmd = [nvcc] + common + ["-c", os.path.join(_CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, _SOURCES))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    link = [nvcc] + NVCC_ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
+        ["-Xlinker", f"-rpath,{cuda_lib}"]
+    r = subprocess.run(link, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    for o in objs:
+        os.remove(o)
+    return LIB_PATH
+
+
+# ---------------------------------------------------------------------------------------------- ctypes
+class Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("decoded_len", "n_blocks", "comp_len", "n_match", "n_seq", "n_tiles")] + \
+               [(n, ctypes.c_uint32) for n in ("block_log2", "tile_log2", "min_match", "flatten", "depth_cap", "max_depth")]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("decoded_len", "comp_len", "n_match", "n_tiles")] + \
+               [(n, ctypes.c_uint32) for n in ("max_depth", "one_pass", "n_levels", "hist_len")] + \
+               [("level_hist", ctypes.c_uint64 * HIST_MAX)]
+
+
+class EncParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("block_log2", "tile_log2", "min_match", "hash_bits", "chain_limit", "flatten", "depth_cap",
+                 "use_first", "min_emit")]
+
+
+# every exported symbol of include/aceapex.h
+SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "aceapex_decode_async",
+           "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
+           "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
+           "aceapex_get_launch_config", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
+           "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
+           "aceapex_encode", "aceapex_free"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libaceapex.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_2606_04268_gb300.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            p, sz, i32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64
+            L.aceapex_peek_header.argtypes = [p, sz, ctypes.POINTER(Info)]
+            L.aceapex_workspace_size.argtypes = [ctypes.POINTER(Info)]
+            L.aceapex_workspace_size.restype = sz
+            L.aceapex_decode.argtypes = [p, sz, p, sz, p]
+            L.aceapex_decode_async.argtypes = [p, sz, p, sz, ctypes.POINTER(Info), p, sz, p, p]
+            L.aceapex_decode_batch.argtypes = [i32, p, p, p, p, p, p]
+            L.aceapex_batch_plan_create.argtypes = [i32, p, p, p, p, p, ctypes.POINTER(p)]
+            L.aceapex_batch_plan_launch.argtypes = [p, i32, p]
+            L.aceapex_batch_plan_statuses.argtypes = [p, p, p]
+            L.aceapex_batch_plan_destroy.argtypes = [p]
+            L.aceapex_set_launch_config.argtypes = [i32, i32, i32]
+            L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
+            L.aceapex_set_force_wavefront.argtypes = [i32]
+            L.aceapex_set_wait_limit.argtypes = [u64, u64]
+            L.aceapex_profile.argtypes = [i32]
+            L.aceapex_profile_read.argtypes = [i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_uint64)]
+            L.aceapex_get_stats.argtypes = [ctypes.POINTER(Stats)]
+            L.aceapex_strerror.argtypes = [i32]
+            L.aceapex_strerror.restype = ctypes.c_char_p
+            L.aceapex_encode.argtypes = [p, sz, ctypes.POINTER(EncParams), ctypes.POINTER(p)]
+            L.aceapex_encode.restype = ctypes.c_int64
+            L.aceapex_free.argtypes = [p]
+            L.aceapex_free.restype = None
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != 0:
+        raise AceapexError(rc, what)
+    return rc
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_ptr(t) -> int:
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.uint8 and t.is_contiguous(), \
+        "expected a contiguous uint8 CUDA tensor"
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------------------------- API
+def strerror(code: int) -> str:
+    return lib().aceapex_strerror(code).decode()
+
+
+def peek_header(prefix) -> Info:
+    a = np.ascontiguousarray(np.frombuffer(prefix, np.uint8) if isinstance(prefix, (bytes, bytearray)) else prefix)
+    info = Info()
+    _check(lib().aceapex_peek_header(a.ctypes.data, a.size, ctypes.byref(info)), "aceapex_peek_header")
+    return info
+
+
+def workspace_size(info: Info) -> int:
+    return lib().aceapex_workspace_size(ctypes.byref(info))
+
+
+def decode_status(comp, out, stream=None) -> int:
+    """Decode device stream `comp` into device buffer `out` (blocking); returns the status code."""
+    return lib().aceapex_decode(_dev_ptr(comp), comp.numel(), _dev_ptr(out) if out.numel() else None,
+                                out.numel(), _stream_ptr(stream))
+
+
+def decode(comp, out, stream=None):
+    _check(decode_status(comp, out, stream), "aceapex_decode")
+    return out
+
+
+def decode_async(comp, out, info: Info, workspace, status, stream=None) -> None:
+    """Enqueue a decode with no host synchronisation; `workspace` is a zero-filled uint8 CUDA tensor of at
+    least workspace_size(info) bytes, `status` an int32 CUDA tensor of one element."""
+    import torch
+    assert status.is_cuda and status.dtype == torch.int32
+    _check(lib().aceapex_decode_async(_dev_ptr(comp), comp.numel(), _dev_ptr(out) if out.numel() else None,
+                                      out.numel(), ctypes.byref(info), _dev_ptr(workspace), workspace.numel(),
+                                      status.data_ptr(), _stream_ptr(stream)), "aceapex_decode_async")
+
+
+def _arrays(comps, outs):
+    n = len(comps)
+    cp = (ctypes.c_void_p * n)(*[_dev_ptr(c) for c in comps])
+    op = (ctypes.c_void_p * n)(*[_dev_ptr(o) if o.numel() else None for o in outs])
+    cl = (ctypes.c_size_t * n)(*[c.numel() for c in comps])
+    ol = (ctypes.c_size_t * n)(*[o.numel() for o in outs])
+    return n, cp, cl, op, ol
+
+
+def decode_batch(comps, outs, stream=None) -> np.ndarray:
+    """Decode many streams (blocking); returns the per-stream status codes."""
+    n, cp, cl, op, ol = _arrays(comps, outs)
+    st = np.zeros(max(n, 1), np.int32)
+    lib().aceapex_decode_batch(n, cp, cl, op, ol, st.ctypes.data, _stream_ptr(stream))
+    return st[:n]
+
+
+class BatchPlan:
+    """Decode plan over fixed buffers: headers read once; launches optionally replayed as a CUDA graph."""
+
+    def __init__(self, comps, outs, stream=None):
+        self._keep = (list(comps), list(outs))
+        n, cp, cl, op, ol = _arrays(comps, outs)
+        self.n = n
+        self._h = ctypes.c_void_p()
+        _check(lib().aceapex_batch_plan_create(n, cp, cl, op, ol, _stream_ptr(stream), ctypes.byref(self._h)),
+               "aceapex_batch_plan_create")
+
+    def launch(self, graph: bool = False, stream=None) -> None:
+        _check(lib().aceapex_batch_plan_launch(self._h, int(graph), _stream_ptr(stream)), "aceapex_batch_plan_launch")
+
+    def statuses(self, stream=None) -> np.ndarray:
+        st = np.zeros(max(self.n, 1), np.int32)
+        lib().aceapex_batch_plan_statuses(self._h, st.ctypes.data, _stream_ptr(stream))
+        return st[:self.n]
+
+    def close(self) -> None:
+        if self._h:
+            lib().aceapex_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_launch_config(threads: int = 256, ctas_per_sm: int = 0, seqs_per_thread: int = 4) -> None:
+    _check(lib().aceapex_set_launch_config(threads, ctas_per_sm, seqs_per_thread), "aceapex_set_launch_config")
+
+
+def get_launch_config():
+    t, c, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().aceapex_get_launch_config(ctypes.byref(t), ctypes.byref(c), ctypes.byref(s)), "get_launch_config")
+    return t.value, c.value, s.value
+
+
+def set_force_wavefront(on: bool) -> None:
+    lib().aceapex_set_force_wavefront(int(on))
+
+
+def set_wait_limit(ns: int = 0, withhold_tile: int | None = None) -> None:
+    """Bounded-wait limit (0 = default 4 s) and the test hook that withholds one tile's flag."""
+    lib().aceapex_set_wait_limit(int(ns), (1 << 64) - 1 if withhold_tile is None else int(withhold_tile))
+
+
+def profile(enable: bool) -> None:
+    """Start (clearing totals) or stop recording CUDA-event times around every library kernel."""
+    lib().aceapex_profile(int(enable))
+
+
+def profile_read() -> dict:
+    """{kernel name: (total ms, launches)} accumulated since profile(True)."""
+    k = 32
+    names = (ctypes.c_char_p * k)()
+    ms = (ctypes.c_double * k)()
+    n = (ctypes.c_uint64 * k)()
+    cnt = lib().aceapex_profile_read(k, names, ms, n)
+    return {names[i].decode(): (ms[i], int(n[i])) for i in range(min(cnt, k))}
+
+
+def get_stats() -> dict:
+    s = Stats()
+    _check(lib().aceapex_get_stats(ctypes.byref(s)), "aceapex_get_stats")
+    return dict(decoded_len=s.decoded_len, comp_len=s.comp_len, n_match=s.n_match, n_tiles=s.n_tiles,
+                max_depth=s.max_depth, one_pass=bool(s.one_pass), n_levels=s.n_levels,
+                level_hist=np.array(s.level_hist[:s.hist_len], dtype=np.uint64))
+
+
+def encode(data, block_log2=20, tile_log2=14, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
+           depth_cap=0, use_first=1, min_emit=0) -> np.ndarray:
+    """Encode host bytes with the library's CPU encoder; returns the stream as a uint8 numpy array."""
+    a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data)
+    assert a.dtype == np.uint8
+    prm = EncParams(block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit)
+    ptr = ctypes.c_void_p()
+    n = lib().aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(prm), ctypes.byref(ptr))
+    if n < 0:
+        raise AceapexError(int(n), "aceapex_encode")
+    out = np.empty(n, np.uint8)
+    ctypes.memmove(out.ctypes.data, ptr, n)
+    lib().aceapex_free(ptr)
+    return out
+
+
+def encode_many(items, threads: int | None = None, **params):
+    """Encode several inputs in parallel threads (the C++ encoder releases the GIL through ctypes)."""
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count()) as ex:
+        return list(ex.map(lambda x: encode(x, **params), items))

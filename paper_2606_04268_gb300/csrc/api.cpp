@@ -1,0 +1,556 @@
+// Host side of the C ABI (include/aceapex.h): header checks, workspace layout and pool, path selection,
+// the batch plan with CUDA-graph replay, statistics.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/aceapex.h"
+#include "decode.h"
+
+using namespace aceapex;
+
+namespace {
+
+// ------------------------------------------------------------------------------------------ header
+uint64_t rd(const uint8_t *p, int n) {
+    uint64_t v = 0;
+    for (int i = n - 1; i >= 0; i--) v = (v << 8) | p[i];
+    return v;
+}
+
+int parse_header(const uint8_t *h, size_t len, aceapex_info *info) {
+    if (!h || !info) return kErrArg;
+    if (len < kStreamHeader) return kErrSize;
+    if (rd(h, 4) != kMagic || rd(h + 4, 2) != kVersion) return kErrFormat;
+    const uint32_t flags = (uint32_t)rd(h + 6, 2);
+    if (flags > 2) return kErrFormat;
+    memset(info, 0, sizeof(*info));
+    info->flatten = flags;
+    info->block_log2 = h[8];
+    info->tile_log2 = h[9];
+    info->min_match = h[10];
+    if (info->block_log2 < kMinBlockLog2 || info->block_log2 > kMaxBlockLog2 || info->tile_log2 < 2 ||
+        info->tile_log2 > info->block_log2 || info->min_match < 1 || h[11] != 0)
+        return kErrFormat;
+    info->depth_cap = (uint32_t)rd(h + 12, 4);
+    info->decoded_len = rd(h + 16, 8);
+    info->n_blocks = rd(h + 24, 8);
+    info->comp_len = rd(h + 32, 8);
+    info->n_match = rd(h + 40, 8);
+    info->max_depth = (uint32_t)rd(h + 48, 4);
+    info->n_seq = rd(h + 56, 8);
+    const uint64_t B = 1ull << info->block_log2;
+    if (info->n_blocks != (info->decoded_len + B - 1) / B) return kErrFormat;
+    if (info->comp_len & 15) return kErrSize;
+    if (info->comp_len < kStreamHeader || info->n_blocks > (info->comp_len - kStreamHeader) / 8) return kErrFormat;
+    if (info->n_match > info->decoded_len || info->n_seq > info->decoded_len) return kErrFormat;
+    info->n_tiles = stream_tiles(info->decoded_len, info->block_log2, info->tile_log2);
+    return kOK;
+}
+
+// ------------------------------------------------------------------------------------------ workspace
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct WsLayout {
+    size_t head, sst, flags, descs, status, block_base, mdst, msrc, mlen, depth, queue, gidx, hist, lvl, cursor, total;
+};
+
+// Regions of a workspace.  One-pass: flags per tile.  Wavefront: per-match records, granule index,
+// per-level arrays.
+WsLayout layout(int n_streams, uint64_t total_tiles, bool wave, const aceapex_info *wi) {
+    WsLayout L{};
+    size_t at = 0;
+    L.head = at; at = up(at + sizeof(WsHead));
+    L.sst = at; at = up(at + sizeof(StreamState) * (size_t)std::max(n_streams, 1));
+    L.status = at; at = up(at + sizeof(int32_t) * (size_t)std::max(n_streams, 1));
+    L.descs = at; at = up(at + (n_streams > 1 ? sizeof(StreamDesc) * (size_t)n_streams : 0));
+    L.flags = at; at = up(at + sizeof(uint32_t) * (size_t)(wave ? 0 : total_tiles));
+    if (wave && wi) {
+        const uint64_t nm = wi->n_match, nb = wi->n_blocks;
+        const uint32_t gl = std::min<uint32_t>(wi->tile_log2, kGranuleLog2);
+        const uint64_t ng = (wi->decoded_len + (1ull << gl) - 1) >> gl;
+        const uint64_t nl = (uint64_t)wi->max_depth + 2;
+        L.block_base = at; at = up(at + 8 * (nb + 1));
+        L.mdst = at; at = up(at + 8 * nm);
+        L.msrc = at; at = up(at + 8 * nm);
+        L.mlen = at; at = up(at + 4 * nm);
+        L.depth = at; at = up(at + 4 * nm);
+        L.queue = at; at = up(at + 4 * nm);
+        L.gidx = at; at = up(at + 4 * ng);
+        L.hist = at; at = up(at + 4 * nl);
+        L.lvl = at; at = up(at + 4 * (nl + 1));
+        L.cursor = at; at = up(at + 4 * nl);
+    }
+    L.total = at;
+    return L;
+}
+
+WaveBufs wave_bufs(uint8_t *ws, const WsLayout &L) {
+    WaveBufs w;
+    w.block_base = (unsigned long long *)(ws + L.block_base);
+    w.mdst = (unsigned long long *)(ws + L.mdst);
+    w.msrc = (unsigned long long *)(ws + L.msrc);
+    w.mlen = (uint32_t *)(ws + L.mlen);
+    w.depth = (uint32_t *)(ws + L.depth);
+    w.queue = (uint32_t *)(ws + L.queue);
+    w.gidx = (uint32_t *)(ws + L.gidx);
+    w.hist = (uint32_t *)(ws + L.hist);
+    w.lvl = (uint32_t *)(ws + L.lvl);
+    w.cursor = (uint32_t *)(ws + L.cursor);
+    return w;
+}
+
+StreamDesc make_desc(const void *comp, void *out, const aceapex_info &I, uint64_t tile_base) {
+    StreamDesc d{};
+    d.comp = (const uint8_t *)comp;
+    d.out = (uint8_t *)out;
+    d.comp_len = I.comp_len;
+    d.N = I.decoded_len;
+    d.n_blocks = I.n_blocks;
+    d.n_seq = I.n_seq;
+    d.n_match = I.n_match;
+    d.tile_base = tile_base;
+    d.n_tiles = I.n_tiles;
+    d.block_log2 = I.block_log2;
+    d.tile_log2 = I.tile_log2;
+    d.min_match = I.min_match;
+    d.max_depth = I.max_depth;
+    return d;
+}
+
+// ------------------------------------------------------------------------------------------ context
+struct DevPool {
+    uint8_t *ws = nullptr;
+    size_t cap = 0;
+    uint8_t *host = nullptr;  // pinned: header read-back, status, level histogram
+    size_t host_cap = 0;
+    int num_sms = 0;
+};
+
+struct Context {
+    std::mutex mu;
+    std::map<int, DevPool> pools;
+    LaunchCfg cfg{0, 256, 4, 0};
+    bool force_wave = false;
+    unsigned long long wait_ns = 4000000000ull;  // bounded device waits give up after 4 s
+    unsigned long long withhold = ~0ull;
+    aceapex_stats stats{};
+};
+Context &ctx() {
+    static Context *c = new Context();  // never destroyed: safe against exit-time ordering
+    return *c;
+}
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return kOK;
+    cudaGetLastError();
+    return kErrCuda;
+}
+
+int pool_for_device(DevPool **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(cudaErrorInvalidDevice);
+    DevPool &p = ctx().pools[dev];
+    if (!p.num_sms) {
+        if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return kErrCuda;
+        p.host_cap = 64 * 1024;
+        if (cudaMallocHost((void **)&p.host, p.host_cap) != cudaSuccess) { p.host = nullptr; return kErrCuda; }
+    }
+    *out = &p;
+    return kOK;
+}
+
+int pool_reserve(DevPool &p, size_t bytes, cudaStream_t stream) {
+    if (bytes <= p.cap) return kOK;
+    if (p.ws) {
+        cudaStreamSynchronize(stream);
+        cudaFree(p.ws);
+        p.ws = nullptr;
+        p.cap = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc((void **)&p.ws, want) != cudaSuccess) { cudaGetLastError(); p.ws = nullptr; return kErrNomem; }
+    // a fresh workspace is zero-filled once: tile flags hold launch epochs and must start below epoch 1
+    if (cudaMemsetAsync(p.ws, 0, want, stream) != cudaSuccess) return kErrCuda;
+    p.cap = want;
+    return kOK;
+}
+
+bool use_wave(const aceapex_info &I) { return I.max_depth > 1 || ctx().force_wave; }
+
+// Enqueue the decode of one stream into workspace ws (layout L); the status goes to status_out.
+int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, const WsLayout &L,
+                int32_t *status_out, int num_sms, cudaStream_t stream) {
+    LaunchCfg cfg = ctx().cfg;
+    cfg.num_sms = num_sms;
+    LaunchArgs a{};
+    a.one = make_desc(comp, out, I, 0);
+    a.n_streams = 1;
+    a.total_tiles = I.n_tiles;
+    a.wait_ns = ctx().wait_ns;
+    a.withhold = ctx().withhold;
+    WsHead *head = (WsHead *)(ws + L.head);
+    StreamState *sst = (StreamState *)(ws + L.sst);
+    cudaError_t e;
+    if (use_wave(I)) e = launch_wave(cfg, head, sst, a, wave_bufs(ws, L), status_out, stream);
+    else e = launch_flat(cfg, head, sst, (uint32_t *)(ws + L.flags), nullptr, a, status_out, stream);
+    return cuda_fail(e);
+}
+
+bool check_ptrs(const void *comp, size_t comp_len, const void *out, size_t out_len) {
+    if (!comp || comp_len < kStreamHeader || ((uintptr_t)comp & 15)) return false;
+    if (!out && out_len) return false;
+    return true;
+}
+
+}  // namespace
+
+// ================================================================================================ C ABI
+extern "C" {
+
+int aceapex_peek_header(const void *host_prefix, size_t len, aceapex_info *info) {
+    return parse_header((const uint8_t *)host_prefix, len, info);
+}
+
+size_t aceapex_workspace_size(const aceapex_info *info) {
+    if (!info) return 0;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    return layout(1, info->n_tiles, use_wave(*info), info).total;
+}
+
+int aceapex_decode(const void *comp, size_t comp_len, void *out, size_t out_len, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!check_ptrs(comp, comp_len, out, out_len)) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    int rc = pool_for_device(&p);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(p->host, comp, kStreamHeader, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return cuda_fail(cudaErrorUnknown);
+    aceapex_info I;
+    rc = parse_header(p->host, kStreamHeader, &I);
+    if (rc) return rc;
+    if (I.comp_len != comp_len || I.decoded_len != out_len) return kErrSize;
+    aceapex_stats &S = ctx().stats;
+    memset(&S, 0, sizeof(S));
+    S.decoded_len = I.decoded_len; S.comp_len = I.comp_len; S.n_match = I.n_match; S.n_tiles = I.n_tiles;
+    S.max_depth = I.max_depth;
+    S.one_pass = !use_wave(I);
+    if (I.decoded_len == 0) return (I.n_blocks || I.n_match || I.n_seq || I.max_depth) ? kErrFormat : kOK;
+    const bool wave = use_wave(I);
+    const WsLayout L = layout(1, I.n_tiles, wave, &I);
+    rc = pool_reserve(*p, L.total, stream);
+    if (rc) return rc;
+    int32_t *d_status = (int32_t *)(p->ws + L.status);
+    rc = enqueue_one(comp, out, I, p->ws, L, d_status, p->num_sms, stream);
+    if (rc) return rc;
+    int32_t *h_status = (int32_t *)p->host;
+    if (cudaMemcpyAsync(h_status, d_status, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return kErrCuda;
+    uint32_t *h_hist = (uint32_t *)(p->host + 64);
+    const uint32_t nh = std::min<uint32_t>(I.max_depth + 1, ACEAPEX_HIST_MAX);
+    if (wave) {
+        if (cudaMemcpyAsync(h_hist, p->ws + L.hist, 4 * nh, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaMemcpyAsync(p->host + 32, p->ws + L.head + offsetof(WsHead, n_levels), 4, cudaMemcpyDeviceToHost,
+                            stream) != cudaSuccess)
+            return kErrCuda;
+    }
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (wave) {
+        S.n_levels = *(uint32_t *)(p->host + 32);
+        S.hist_len = nh;
+        for (uint32_t k = 0; k < nh; k++) S.level_hist[k] = h_hist[k];
+    }
+    return *h_status;
+}
+
+int aceapex_decode_async(const void *comp, size_t comp_len, void *out, size_t out_len, const aceapex_info *info,
+                         void *d_ws, size_t ws_len, int32_t *d_status, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!check_ptrs(comp, comp_len, out, out_len) || !info || !d_status || ((uintptr_t)d_ws & 15)) return kErrArg;
+    if (info->comp_len != comp_len || info->decoded_len != out_len) return kErrSize;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    int rc = pool_for_device(&p);
+    if (rc) return rc;
+    if (info->decoded_len == 0) return cuda_fail(cudaMemsetAsync(d_status, 0, 4, stream));
+    const WsLayout L = layout(1, info->n_tiles, use_wave(*info), info);
+    if (!d_ws || ws_len < L.total) return kErrNomem;
+    return enqueue_one(comp, out, *info, (uint8_t *)d_ws, L, d_status, p->num_sms, stream);
+}
+
+// ------------------------------------------------------------------------------------------ batch
+struct aceapex_batch_plan {
+    int n = 0;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<int32_t> arg_status;       // status known on the host (argument / header errors)
+    std::vector<int> flat_idx, wave_idx;    // stream indices per path
+    std::vector<aceapex_info> info;
+    std::vector<const void *> comps;
+    std::vector<void *> outs;
+    LaunchArgs flat_args{};
+    uint8_t *ws = nullptr;                 // flat workspace: head, states, statuses, descriptors, flags
+    WsLayout flat_L{};
+    uint8_t *wave_ws = nullptr;            // shared by the wave streams, decoded one after another
+    size_t wave_cap = 0;
+    int32_t *wave_status = nullptr;        // one device status per wave stream
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+// Read the 64-byte header of every stream back to the host (one small copy per stream, one sync).
+static int read_headers(int n, const void *const *comps, std::vector<uint8_t> &hdr, cudaStream_t stream) {
+    uint8_t *pinned = nullptr;
+    if (cudaMallocHost((void **)&pinned, (size_t)n * kStreamHeader) != cudaSuccess) return kErrNomem;
+    for (int i = 0; i < n; i++) {
+        if (!comps[i]) continue;
+        if (cudaMemcpyAsync(pinned + (size_t)i * kStreamHeader, comps[i], kStreamHeader, cudaMemcpyDeviceToHost,
+                            stream) != cudaSuccess) {
+            cudaFreeHost(pinned);
+            return cuda_fail(cudaErrorUnknown);
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) hdr.assign(pinned, pinned + (size_t)n * kStreamHeader);
+    cudaFreeHost(pinned);
+    return cuda_fail(e);
+}
+
+int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *comp_lens, void *const *outs,
+                              const size_t *out_lens, void *stream_, aceapex_batch_plan **plan_out) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (n < 0 || (n > 0 && (!comps || !comp_lens || !outs || !out_lens)) || !plan_out) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    int rc = pool_for_device(&p);
+    if (rc) return rc;
+    aceapex_batch_plan *P = new (std::nothrow) aceapex_batch_plan();
+    if (!P) return kErrNomem;
+    P->n = n;
+    cudaGetDevice(&P->device);
+    P->num_sms = p->num_sms;
+    P->arg_status.assign(n, 0);
+    P->info.resize(n);
+    P->comps.assign(comps, comps + n);
+    P->outs.assign(outs, outs + n);
+    std::vector<const void *> valid(n, nullptr);
+    for (int i = 0; i < n; i++) {
+        if (!check_ptrs(comps[i], comp_lens[i], outs[i], out_lens[i])) P->arg_status[i] = kErrArg;
+        else valid[i] = comps[i];
+    }
+    std::vector<uint8_t> hdr;
+    rc = read_headers(n, valid.data(), hdr, stream);
+    if (rc) { delete P; return rc; }
+    std::vector<StreamDesc> descs;
+    uint64_t tiles = 0;
+    size_t wave_need = 0;
+    for (int i = 0; i < n; i++) {
+        if (P->arg_status[i]) continue;
+        aceapex_info &I = P->info[i];
+        int r = parse_header(hdr.data() + (size_t)i * kStreamHeader, kStreamHeader, &I);
+        if (!r && (I.comp_len != comp_lens[i] || I.decoded_len != out_lens[i])) r = kErrSize;
+        if (!r && I.decoded_len == 0 && (I.n_blocks || I.n_match || I.n_seq || I.max_depth)) r = kErrFormat;
+        if (r) { P->arg_status[i] = r; continue; }
+        if (I.decoded_len == 0) continue;  // nothing to do, status 0
+        if (use_wave(I)) {
+            P->wave_idx.push_back(i);
+            wave_need = std::max(wave_need, layout(1, I.n_tiles, true, &I).total);
+        } else {
+            P->flat_idx.push_back(i);
+            descs.push_back(make_desc(comps[i], outs[i], I, tiles));
+            tiles += I.n_tiles;
+        }
+    }
+    const int nf = (int)P->flat_idx.size();
+    P->flat_L = layout(std::max(nf, 2), tiles, false, nullptr);  // >= 2: the descriptor table always lives in memory
+    if (nf > 0) {
+        if (cudaMalloc((void **)&P->ws, P->flat_L.total) != cudaSuccess) { cudaGetLastError(); delete P; return kErrNomem; }
+        cudaMemsetAsync(P->ws, 0, P->flat_L.total, stream);
+        cudaMemcpyAsync(P->ws + P->flat_L.descs, descs.data(), sizeof(StreamDesc) * nf, cudaMemcpyHostToDevice, stream);
+        P->flat_args.n_streams = nf;
+        P->flat_args.total_tiles = tiles;
+        if (nf == 1) P->flat_args.one = descs[0];
+    }
+    if (!P->wave_idx.empty()) {
+        P->wave_cap = wave_need;
+        if (cudaMalloc((void **)&P->wave_ws, wave_need) != cudaSuccess ||
+            cudaMalloc((void **)&P->wave_status, 4 * P->wave_idx.size()) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(P->ws); cudaFree(P->wave_ws);
+            delete P;
+            return kErrNomem;
+        }
+        cudaMemsetAsync(P->wave_ws, 0, wave_need, stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) { cudaFree(P->ws); cudaFree(P->wave_ws); cudaFree(P->wave_status); delete P; return cuda_fail(e); }
+    *plan_out = P;
+    return kOK;
+}
+
+static int plan_enqueue(aceapex_batch_plan *P, cudaStream_t stream) {
+    LaunchCfg cfg = ctx().cfg;
+    cfg.num_sms = P->num_sms;
+    if (!P->flat_idx.empty()) {
+        P->flat_args.wait_ns = ctx().wait_ns;
+        P->flat_args.withhold = ctx().withhold;
+        uint8_t *ws = P->ws;
+        const WsLayout &L = P->flat_L;
+        const StreamDesc *descs = P->flat_args.n_streams > 1 ? (const StreamDesc *)(ws + L.descs) : nullptr;
+        cudaError_t e = launch_flat(cfg, (WsHead *)(ws + L.head), (StreamState *)(ws + L.sst), (uint32_t *)(ws + L.flags),
+                                    descs, P->flat_args, (int32_t *)(ws + L.status), stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    for (size_t k = 0; k < P->wave_idx.size(); k++) {
+        const int i = P->wave_idx[k];
+        const aceapex_info &I = P->info[i];
+        const WsLayout L = layout(1, I.n_tiles, true, &I);
+        int rc = enqueue_one(P->comps[i], P->outs[i], I, P->wave_ws, L, P->wave_status + k, P->num_sms, stream);
+        if (rc) return rc;
+    }
+    return kOK;
+}
+
+int aceapex_batch_plan_launch(aceapex_batch_plan *P, int graph, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!P) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    if (!graph) return plan_enqueue(P, stream);
+    if (!P->exec) {
+        if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+        int rc = plan_enqueue(P, stream);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(stream, &gr);
+        if (rc || e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return rc ? rc : cuda_fail(e); }
+        e = cudaGraphInstantiate(&P->exec, gr, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(gr); P->exec = nullptr; return cuda_fail(e); }
+        P->graph = gr;
+    }
+    return cuda_fail(cudaGraphLaunch(P->exec, stream));
+}
+
+int aceapex_batch_plan_statuses(aceapex_batch_plan *P, int32_t *statuses, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!P || (!statuses && P->n)) return kErrArg;
+    std::vector<int32_t> fs(P->flat_idx.size()), wsts(P->wave_idx.size());
+    if (!fs.empty() && cudaMemcpyAsync(fs.data(), P->ws + P->flat_L.status, 4 * fs.size(), cudaMemcpyDeviceToHost,
+                                       stream) != cudaSuccess)
+        return cuda_fail(cudaErrorUnknown);
+    if (!wsts.empty() &&
+        cudaMemcpyAsync(wsts.data(), P->wave_status, 4 * wsts.size(), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return cuda_fail(cudaErrorUnknown);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int first = 0;
+    for (int i = 0; i < P->n; i++) statuses[i] = P->arg_status[i];
+    for (size_t k = 0; k < fs.size(); k++) statuses[P->flat_idx[k]] = fs[k];
+    for (size_t k = 0; k < wsts.size(); k++) statuses[P->wave_idx[k]] = wsts[k];
+    for (int i = 0; i < P->n; i++) if (statuses[i] && !first) first = statuses[i];
+    return first;
+}
+
+int aceapex_batch_plan_destroy(aceapex_batch_plan *P) {
+    if (!P) return kErrArg;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    cudaFree(P->ws);
+    cudaFree(P->wave_ws);
+    cudaFree(P->wave_status);
+    delete P;
+    return kOK;
+}
+
+int aceapex_decode_batch(int n, const void *const *comps, const size_t *comp_lens, void *const *outs,
+                         const size_t *out_lens, int32_t *statuses, void *stream) {
+    if (n < 0 || (n > 0 && !statuses)) return kErrArg;
+    aceapex_batch_plan *P = nullptr;
+    int rc = aceapex_batch_plan_create(n, comps, comp_lens, outs, out_lens, stream, &P);
+    if (rc) return rc;
+    rc = aceapex_batch_plan_launch(P, 0, stream);
+    int rs = rc ? rc : aceapex_batch_plan_statuses(P, statuses, stream);
+    aceapex_batch_plan_destroy(P);
+    return rs;
+}
+
+// ------------------------------------------------------------------------------------------ config, stats
+int aceapex_set_launch_config(int threads, int ctas_per_sm, int spt) {
+    const bool ok = (threads == 128 && (spt == 4 || spt == 8)) || (threads == 256 && (spt == 2 || spt == 4 || spt == 8)) ||
+                    (threads == 512 && (spt == 2 || spt == 4));
+    if (!ok || ctas_per_sm < 0) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    ctx().cfg.threads = threads;
+    ctx().cfg.ctas_per_sm = ctas_per_sm;
+    ctx().cfg.spt = spt;
+    return kOK;
+}
+
+int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *spt) {
+    if (!threads || !ctas_per_sm || !spt) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    *threads = ctx().cfg.threads;
+    *ctas_per_sm = ctx().cfg.ctas_per_sm;
+    *spt = ctx().cfg.spt;
+    return kOK;
+}
+
+int aceapex_set_force_wavefront(int on) {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    ctx().force_wave = on != 0;
+    return kOK;
+}
+
+int aceapex_set_wait_limit(uint64_t ns, uint64_t withhold_tile) {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    ctx().wait_ns = ns ? ns : 4000000000ull;
+    ctx().withhold = withhold_tile;
+    return kOK;
+}
+
+int aceapex_profile(int enable) {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    prof_enable(enable != 0);
+    return kOK;
+}
+
+int aceapex_profile_read(int max_kernels, const char **names, double *total_ms, uint64_t *launches) {
+    if (max_kernels < 0 || (max_kernels > 0 && (!names || !total_ms || !launches))) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    double ms[kKCount];
+    unsigned long long n[kKCount];
+    prof_collect(ms, n);
+    const int k = std::min(max_kernels, (int)kKCount);
+    for (int i = 0; i < k; i++) { names[i] = kKernelNames[i]; total_ms[i] = ms[i]; launches[i] = n[i]; }
+    return kKCount;
+}
+
+int aceapex_get_stats(aceapex_stats *s) {
+    if (!s) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    *s = ctx().stats;
+    return kOK;
+}
+
+const char *aceapex_strerror(int code) {
+    switch (code) {
+        case kOK: return "ok";
+        case kErrArg: return "invalid argument";
+        case kErrFormat: return "malformed stream";
+        case kErrSize: return "size mismatch";
+        case kErrOffset: return "match offset out of range";
+        case kErrTimeout: return "device wait timed out";
+        case kErrCuda: return "CUDA runtime error";
+        case kErrNomem: return "out of memory / workspace too small";
+        case kErrDepth: return "match depth above the stream's max_depth";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,517 @@
+// ACEAPEX decode kernels for sm_103a and their host-side launch sequences.
+//
+// One-pass path (every match has depth <= 1, i.e. reads only literal bytes: chain flattening, §3.3):
+//   k_flat -- persistent CTAs take tiles from a global ticket queue (one queue over all the streams of a
+//   batch).  Phase A parses the tile and writes its literal bytes, then publishes a per-tile flag.  Phase B
+//   waits (bounded) until every earlier tile of the same stream has published, re-parses the tile (its
+//   varints are still in L2) and copies its matches from absolute offsets (§3.1).  Tickets are handed out
+//   in order and phase A never waits, so the wait always ends; no per-match metadata reaches HBM.
+//
+// Wavefront path (§7.1, any depth): k_parse writes the literals and one record (destination, source,
+//   length) per match plus a granule index that finds the writers of any byte range; k_depth computes each
+//   match's depth = 1 + the largest depth among the matches that wrote its source (a ticketed dataflow
+//   over match indices, whose dependencies always point to smaller indices); k_hist/k_levels/k_scatter
+//   bucket the matches into per-level queues; k_wave, one cooperative persistent launch, drains level 1,
+//   2, ... with a bounded grid barrier between levels, instead of one kernel launch per level as in the
+//   paper's H100 design.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "decode.h"
+#include "tile.cuh"
+
+namespace aceapex {
+
+
+// ------------------------------------------------------------------------------------------ reset
+__global__ void k_reset(WsHead *head, StreamState *sst, const StreamDesc *descs, LaunchArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        head->epoch = head->epoch + 1 == 0 ? 1 : head->epoch + 1;
+        head->ticket = 0; head->ticket2 = 0; head->bar_count = 0; head->bar_gen = 0;
+        head->depth_seen = 0; head->n_levels = 0;
+    }
+    if (i < a.n_streams) {
+        const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[i];
+        sst[i].front = sd.tile_base; sst[i].seq_sum = 0; sst[i].match_sum = 0; sst[i].depth_max = 0;
+        sst[i].status = 0; sst[i].err_key = ~0ull;
+    }
+}
+
+// Header totals against the blocks' fields, then the status out (async API).
+__global__ void k_finalize(StreamState *sst, const StreamDesc *descs, LaunchArgs a, int32_t *status_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_streams) return;
+    const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[i];
+    StreamState &st = sst[i];
+    if (st.err_key == ~0ull && (st.seq_sum != sd.n_seq || st.match_sum != sd.n_match || st.depth_max != sd.max_depth))
+        st.err_key = (kOrderTotals << 4) | (unsigned long long)(-kErrFormat);
+    st.status = st.err_key == ~0ull ? 0 : -(int)(st.err_key & 15);
+    if (status_out) status_out[i] = st.status;
+}
+
+__device__ __forceinline__ int find_stream(const StreamDesc *descs, int n, uint64_t t) {
+    int a = 0, z = n;
+    while (z - a > 1) {
+        const int mid = (a + z) >> 1;
+        if (descs[mid].tile_base <= t) a = mid; else z = mid;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------------------------------------ one-pass kernel
+template <int NT, int SPT>
+__global__ void __launch_bounds__(NT) k_flat(WsHead *head, StreamState *sst, uint32_t *flags, const StreamDesc *descs,
+                                             LaunchArgs a) {
+    __shared__ TileSmem<NT, SPT> sm;
+    __shared__ unsigned long long s_t;
+    __shared__ int s_si;
+    const uint32_t epoch = head->epoch;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_t = atomicAdd(&head->ticket, 1ull);
+            s_si = (s_t < a.total_tiles) ? (a.n_streams == 1 ? 0 : find_stream(descs, a.n_streams, s_t)) : 0;
+        }
+        __syncthreads();
+        const unsigned long long t = s_t;
+        if (t >= a.total_tiles) break;
+        const int si = s_si;
+        const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[si];
+        StreamState *st = &sst[si];
+        if (threadIdx.x == 0) {
+            const uint64_t lt = t - sd.tile_base;
+            const uint32_t sh = sd.block_log2 - sd.tile_log2;
+            sm.err = 0; sm.verr = 0;
+            // a stream that already failed is skipped (its flags are still published below)
+            sm.err = *(volatile int *)&st->status ? 1 : tile_open(sm, sd, lt >> sh, (uint32_t)(lt & ((1ull << sh) - 1)), st);
+        }
+        __syncthreads();
+        // phase A: literals
+        if (!sm.err) {
+            tile_rewind(sm);
+            while (sm.seq < sm.seq_end) {
+                if (!chunk_parse(sm, false)) break;
+                chunk_literals(sm, sd.out);
+                __syncthreads();
+            }
+        }
+        // publish this tile's literals
+        __threadfence();
+        __syncthreads();
+        const int err_a = sm.err;  // negative: a format error of this tile; 1: the stream failed earlier
+        const unsigned long long order = t - sd.tile_base;
+        if (threadIdx.x == 0) {
+            if (err_a < 0) report(st, err_a, order);
+            if (t != a.withhold) st_release_u32(&flags[t], epoch);
+        }
+        // phase B: wait for the literals of every earlier tile of this stream, then copy the matches
+        if (!err_a) {
+            if (threadIdx.x < 32) {
+                unsigned long long f = ld_acquire_u64(&st->front);
+                if (f < sd.tile_base) f = sd.tile_base;
+                const uint64_t t0 = global_ns();
+                bool timed_out = false;
+                while (f < t) {
+                    const unsigned long long k = f + threadIdx.x;
+                    const bool done = k >= t || ld_acquire_u32(&flags[k]) == epoch;
+                    const unsigned ball = __ballot_sync(0xffffffffu, done);
+                    if (ball == 0xffffffffu) { f += 32; continue; }
+                    f += __ffs(~ball) - 1;
+                    if (global_ns() - t0 > a.wait_ns) { timed_out = true; break; }
+                    __nanosleep(64);
+                }
+                if (threadIdx.x == 0) {
+                    if (timed_out) { report(st, kErrTimeout, kOrderTimeout); sm.err = kErrTimeout; }
+                    else atomicMax(&st->front, t < f ? t : f);
+                }
+            }
+            __syncthreads();
+            if (!sm.err) {
+                tile_rewind(sm);
+                while (sm.seq < sm.seq_end) {
+                    if (!chunk_parse(sm, true)) break;
+                    chunk_matches(sm, sd.out);
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0 && sm.err) report(st, sm.err, order);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------ wavefront path
+constexpr int kNT = 256, kSPT = 4;
+
+// Prefix sum of the blocks' match counts (one CTA); block_base[n_blocks] = total, which must equal the
+// header's n_match (the record arrays are sized from it).
+__global__ void __launch_bounds__(kNT) k_match_base(StreamState *sst, LaunchArgs a, unsigned long long *block_base) {
+    __shared__ ScanSmem<kNT> scan;
+    __shared__ unsigned int s_depth;
+    const StreamDesc &sd = a.one;
+    if (threadIdx.x == 0) s_depth = 0;
+    __syncthreads();
+    unsigned long long run = 0;
+    for (uint64_t b0 = 0; b0 < sd.n_blocks; b0 += kNT) {
+        const uint64_t b = b0 + threadIdx.x;
+        unsigned long long nm = 0;
+        if (b < sd.n_blocks) {
+            const uint64_t boff = ld64(sd.comp + kStreamHeader + 8 * b);
+            if ((boff & 15) == 0 && boff + kBlockHeader <= sd.comp_len) {
+                nm = ld32(sd.comp + boff + 4);
+                atomicMax(&s_depth, ld32(sd.comp + boff + 24));
+            } else {
+                report(&sst[0], kErrFormat, b << (sd.block_log2 - sd.tile_log2));
+            }
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan<kNT>(nm, scan, tot);
+        if (b < sd.n_blocks) block_base[b] = run + ex;
+        run += tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        block_base[sd.n_blocks] = run;
+        // header totals against the blocks, before any depth is computed (the level arrays are sized
+        // from the header's max_depth)
+        if (run != sd.n_match || s_depth != sd.max_depth) report(&sst[0], kErrFormat, kOrderTotals);
+    }
+}
+
+// Parse every tile: literals to `out`, one record per match that starts in the tile, granule index.
+__global__ void __launch_bounds__(kNT) k_parse(StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    __shared__ TileSmem<kNT, kSPT> sm;
+    const StreamDesc &sd = a.one;
+    StreamState *st = &sst[0];
+    const uint32_t sh = sd.block_log2 - sd.tile_log2;
+    const uint32_t gl = sd.tile_log2 < kGranuleLog2 ? sd.tile_log2 : kGranuleLog2;
+    for (uint64_t t = blockIdx.x; t < sd.n_tiles; t += gridDim.x) {
+        const uint64_t b = t >> sh;
+        if (threadIdx.x == 0) {
+            sm.err = 0; sm.verr = 0;
+            sm.err = *(volatile int *)&st->status ? 1 : tile_open(sm, sd, b, (uint32_t)(t & ((1ull << sh) - 1)), st);
+        }
+        __syncthreads();
+        if (sm.err) { if (threadIdx.x == 0 && sm.err < 0) report(st, sm.err, t); return; }
+        tile_rewind(sm);
+        const unsigned long long mb = wb.block_base[b], mb_next = wb.block_base[b + 1];
+        while (sm.seq < sm.seq_end) {
+            if (!chunk_parse(sm, true)) break;
+            chunk_literals(sm, sd.out);
+            const uint32_t n = sm.chunk_n, nm = sm.chunk_nm, cs = sm.chunk_seq;
+            // match records: owned by the tile that holds the match's first byte
+            for (uint32_t i = threadIdx.x; i < nm; i += kNT) {
+                const uint32_t drel = sm.start[i] + sm.rlen[i];
+                if (drel >= sm.tile_lo && drel < sm.tile_hi) {
+                    const unsigned long long m = mb + cs + i;
+                    if (m < mb_next && m < sd.n_match) {
+                        wb.mdst[m] = sm.b0 + drel;
+                        wb.msrc[m] = sm.soff[i];
+                        wb.mlen[m] = sm.mlen[i];
+                        wb.depth[m] = 0;
+                    } else {
+                        report(st, kErrFormat, t);
+                    }
+                }
+            }
+            // granule index: gidx[g] = first match whose range ends after the granule's first byte
+            const uint32_t G = 1u << gl;
+            uint32_t lo = sm.start[0] > sm.tile_lo ? sm.start[0] : sm.tile_lo;
+            const uint32_t hi = sm.start[n] < sm.tile_hi ? sm.start[n] : sm.tile_hi;
+            lo = (lo + G - 1) & ~(G - 1);
+            for (uint32_t q = lo + threadIdx.x * G; q < hi; q += kNT * G) {
+                const uint32_t i = seq_of(sm, n, q);
+                wb.gidx[(sm.b0 + q) >> gl] = (i < nm) ? (uint32_t)(mb + cs + i) : (uint32_t)mb_next;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && sm.err) report(st, sm.err, t);
+        __syncthreads();
+    }
+}
+
+// Depth of every match (§7.1): 1 + the largest depth among the matches that wrote its effective source
+// [s, s + min(L, d - s)); literal bytes count as depth 0.  Chunks of kNT matches are taken in index order;
+// a writer always has a smaller index than its reader, so the lowest unfinished chunk can always finish.
+__global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    __shared__ unsigned long long s_c;
+    __shared__ int s_abort;
+    const StreamDesc &sd = a.one;
+    const uint64_t nmatch = sd.n_match;
+    const uint32_t gl = sd.tile_log2 < kGranuleLog2 ? sd.tile_log2 : kGranuleLog2;
+    const uint32_t cap = sd.max_depth;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (threadIdx.x == 0) { s_c = atomicAdd(&head->ticket2, 1ull); s_abort = 0; }
+        __syncthreads();
+        const uint64_t m = s_c * kNT + threadIdx.x;
+        if (s_c * kNT >= nmatch) break;
+        bool done = m >= nmatch;
+        uint64_t s = 0, send = 0, w = 0;
+        uint32_t mx = 0;
+        if (!done) {
+            const uint64_t d = wb.mdst[m];
+            s = wb.msrc[m];
+            const uint64_t L = wb.mlen[m];
+            if (s < d && d <= sd.N) {  // records are checked by k_parse; stale ones (after an error) read nothing
+                send = s + (L < d - s ? L : d - s);
+                w = wb.gidx[s >> gl];
+                while (w < m && wb.mdst[w] + wb.mlen[w] <= s) w++;
+            } else {
+                s = send = 0; w = m;
+            }
+        }
+        int iter = 0;
+        while (__syncthreads_or(!done)) {
+            if (!done) {
+                // advance over writers whose depth is known; stop at the first unknown one
+                while (w < m && wb.mdst[w] < send) {
+                    const uint32_t dw = ld_relaxed_u32(&wb.depth[w]);
+                    if (dw == 0) break;
+                    mx = dw > mx ? dw : mx;
+                    w++;
+                }
+                if (!(w < m && wb.mdst[w] < send)) {
+                    uint32_t dep = mx + 1;
+                    if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
+                    st_relaxed_u32(&wb.depth[m], dep);
+                    atomicMax(&head->depth_seen, dep);
+                    done = true;
+                }
+            }
+            if (++iter % 64 == 0 && threadIdx.x == 0 && global_ns() - t0 > a.wait_ns) {
+                report(&sst[0], kErrTimeout, kOrderTimeout);
+                s_abort = 1;
+            }
+            __syncthreads();
+            if (s_abort) return;
+        }
+    }
+}
+
+// Level histogram (shared-memory privatised for the first kHistSmem levels).
+constexpr int kHistSmem = 2048;
+__global__ void __launch_bounds__(kNT) k_hist(LaunchArgs a, WaveBufs wb) {
+    __shared__ unsigned int h[kHistSmem];
+    for (int i = threadIdx.x; i < kHistSmem; i += kNT) h[i] = 0;
+    __syncthreads();
+    const uint64_t n = a.one.n_match;
+    for (uint64_t m = (uint64_t)blockIdx.x * kNT + threadIdx.x; m < n; m += (uint64_t)gridDim.x * kNT) {
+        const uint32_t d = wb.depth[m];
+        if (d > a.one.max_depth) continue;  // only after an error (k_depth clamps to max_depth)
+        if (d < kHistSmem) atomicAdd(&h[d], 1u);
+        else atomicAdd(&wb.hist[d], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHistSmem && i <= (int)a.one.max_depth; i += kNT)
+        if (h[i]) atomicAdd(&wb.hist[i], h[i]);
+}
+
+// Exclusive scan of the histogram into level offsets; cursor = offsets.
+__global__ void __launch_bounds__(kNT) k_levels(WsHead *head, LaunchArgs a, WaveBufs wb) {
+    __shared__ ScanSmem<kNT> scan;
+    const uint32_t nl = a.one.max_depth + 1;  // levels 0..max_depth
+    unsigned long long run = 0;
+    for (uint32_t k0 = 0; k0 < nl; k0 += kNT) {
+        const uint32_t k = k0 + threadIdx.x;
+        const unsigned long long v = k < nl ? wb.hist[k] : 0;
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan<kNT>(v, scan, tot);
+        if (k < nl) { wb.lvl[k] = (uint32_t)(run + ex); wb.cursor[k] = (uint32_t)(run + ex); }
+        run += tot;
+    }
+    if (threadIdx.x == 0) { wb.lvl[nl] = (uint32_t)run; head->n_levels = head->depth_seen; }
+}
+
+__global__ void __launch_bounds__(kNT) k_scatter(LaunchArgs a, WaveBufs wb) {
+    const uint64_t n = a.one.n_match;
+    for (uint64_t m = (uint64_t)blockIdx.x * kNT + threadIdx.x; m < n; m += (uint64_t)gridDim.x * kNT) {
+        const uint32_t d = wb.depth[m];
+        if (d > a.one.max_depth) continue;
+        const unsigned peers = __match_any_sync(__activemask(), d);
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1));
+        uint32_t base = 0;
+        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&wb.cursor[d], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        wb.queue[base + rank] = (uint32_t)m;
+    }
+}
+
+// Bounded grid barrier of a cooperative launch.  Returns false when the wait timed out.
+__device__ bool grid_barrier(WsHead *head, StreamState *st, uint64_t t0, uint64_t wait_ns) {
+    __shared__ int s_ok;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        const unsigned gen = ld_acquire_u32(&head->bar_gen);
+        const unsigned arrived = atomicAdd(&head->bar_count, 1u) + 1;
+        if (arrived == gridDim.x) {
+            atomicExch(&head->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&head->bar_gen, gen + 1);
+        } else {
+            while (ld_acquire_u32(&head->bar_gen) == gen) {
+                if (global_ns() - t0 > wait_ns) { report(st, kErrTimeout, kOrderTimeout); s_ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+    }
+    __syncthreads();
+    return s_ok;
+}
+
+// Drain the per-level queues, level 1 first; one warp copies one match, lanes over 32-byte strides,
+// out[d+k] = out[s + (k mod (d-s))] so that a self-overlapping copy never reads its own output.
+__global__ void __launch_bounds__(kNT) k_wave(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    const uint32_t nlev = head->depth_seen;
+    const uint64_t t0 = global_ns();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * kNT + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * kNT) >> 5;
+    uint8_t *out = a.one.out;
+    for (uint32_t k = 1; k <= nlev; k++) {
+        const uint32_t beg = wb.lvl[k], end = wb.lvl[k + 1];
+        for (uint64_t i = beg + warp; i < end; i += nwarps) {
+            const uint32_t m = wb.queue[i];
+            if (m >= a.one.n_match) continue;
+            const uint64_t d = wb.mdst[m], s = wb.msrc[m], L = wb.mlen[m], p = d - s;
+            if (s >= d || d + L > a.one.N) continue;  // never true for records k_parse checked
+            for (uint64_t j = lane; j < L; j += 32) out[d + j] = ld_out(out + s + (j < p ? j : j % p));
+        }
+        if (k < nlev && !grid_barrier(head, &sst[0], t0, a.wait_ns)) return;
+    }
+}
+
+// ------------------------------------------------------------------------------------------ host side
+const char *const kKernelNames[kKCount] = {"k_reset", "k_flat", "k_finalize", "k_match_base", "k_parse",
+                                           "k_depth", "k_hist", "k_levels", "k_scatter", "k_wave"};
+namespace {
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<int> ids;  // kernel id of each recorded (start, stop) pair
+    double ms[kKCount] = {};
+    unsigned long long launches[kKCount] = {};
+};
+Prof &prof() {
+    static Prof *p = new Prof();
+    return *p;
+}
+cudaEvent_t prof_event() {
+    Prof &P = prof();
+    if (P.used == P.pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        P.pool.push_back(e);
+    }
+    return P.pool[P.used++];
+}
+}  // namespace
+
+void prof_enable(bool on) {
+    Prof &P = prof();
+    P.on = on;
+    P.used = 0;
+    P.ids.clear();
+    for (int i = 0; i < kKCount; i++) { P.ms[i] = 0; P.launches[i] = 0; }
+}
+bool prof_enabled() { return prof().on; }
+void prof_mark(int id, bool start, cudaStream_t stream) {
+    Prof &P = prof();
+    if (!P.on) return;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+    if (start) P.ids.push_back(id);
+    cudaEventRecord(prof_event(), stream);
+}
+int prof_collect(double *ms, unsigned long long *launches) {
+    Prof &P = prof();
+    for (size_t k = 0; k < P.ids.size() && 2 * k + 1 < P.used; k++) {
+        cudaEventSynchronize(P.pool[2 * k + 1]);
+        float t = 0;
+        cudaEventElapsedTime(&t, P.pool[2 * k], P.pool[2 * k + 1]);
+        P.ms[P.ids[k]] += t;
+        P.launches[P.ids[k]] += 1;
+    }
+    P.used = 0;
+    P.ids.clear();
+    for (int i = 0; i < kKCount; i++) { ms[i] = P.ms[i]; launches[i] = P.launches[i]; }
+    return kKCount;
+}
+
+#define PROF(id, ...) do { prof_mark(id, true, stream); __VA_ARGS__; prof_mark(id, false, stream); } while (0)
+
+template <int NT, int SPT>
+static cudaError_t launch_flat_t(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags,
+                                 const StreamDesc *descs, const LaunchArgs &a, cudaStream_t stream) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat<NT, SPT>, NT, 0);
+    if (e != cudaSuccess) return e;
+    if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
+    if (occ < 1) occ = 1;
+    uint64_t grid = (uint64_t)occ * cfg.num_sms;
+    if (grid > a.total_tiles) grid = a.total_tiles;
+    if (grid < 1) grid = 1;
+    PROF(kKFlat, k_flat<NT, SPT><<<(unsigned)grid, NT, 0, stream>>>(head, sst, flags, descs, a));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flat(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags, const StreamDesc *descs,
+                        const LaunchArgs &a, int32_t *status_out, cudaStream_t stream) {
+    const int ns = a.n_streams;
+    PROF(kKReset, k_reset<<<(ns + 255) / 256, 256, 0, stream>>>(head, sst, descs, a));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.total_tiles > 0) {
+#define ACEAPEX_FLAT(NT_, SPT_) \
+    if (cfg.threads == NT_ && cfg.spt == SPT_) e = launch_flat_t<NT_, SPT_>(cfg, head, sst, flags, descs, a, stream); else
+        ACEAPEX_FLAT(128, 4) ACEAPEX_FLAT(128, 8) ACEAPEX_FLAT(256, 2) ACEAPEX_FLAT(256, 4) ACEAPEX_FLAT(256, 8)
+        ACEAPEX_FLAT(512, 2) ACEAPEX_FLAT(512, 4)
+        e = launch_flat_t<256, 4>(cfg, head, sst, flags, descs, a, stream);
+#undef ACEAPEX_FLAT
+        if (e != cudaSuccess) return e;
+    }
+    PROF(kKFinalize, k_finalize<<<(ns + 255) / 256, 256, 0, stream>>>(sst, descs, a, status_out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, const LaunchArgs &a, const WaveBufs &wb,
+                        int32_t *status_out, cudaStream_t stream) {
+    PROF(kKReset, k_reset<<<1, 256, 0, stream>>>(head, sst, nullptr, a));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const StreamDesc &sd = a.one;
+    if (sd.N > 0) {
+        cudaMemsetAsync(wb.hist, 0, sizeof(uint32_t) * (sd.max_depth + 2), stream);
+        PROF(kKMatchBase, k_match_base<<<1, kNT, 0, stream>>>(sst, a, wb.block_base));
+        const uint64_t ptiles = std::min<uint64_t>(sd.n_tiles, (uint64_t)cfg.num_sms * 8);
+        PROF(kKParse, k_parse<<<(unsigned)std::max<uint64_t>(ptiles, 1), kNT, 0, stream>>>(sst, a, wb));
+        if (sd.n_match > 0) {
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_depth, kNT, 0);
+            const uint64_t chunks = (sd.n_match + kNT - 1) / kNT;
+            const uint64_t dgrid = std::min<uint64_t>(chunks, (uint64_t)std::max(occ, 1) * cfg.num_sms);
+            PROF(kKDepth, k_depth<<<(unsigned)dgrid, kNT, 0, stream>>>(head, sst, a, wb));
+            const unsigned g = (unsigned)std::min<uint64_t>(chunks, (uint64_t)cfg.num_sms * 4);
+            PROF(kKHist, k_hist<<<g, kNT, 0, stream>>>(a, wb));
+            PROF(kKLevels, k_levels<<<1, kNT, 0, stream>>>(head, a, wb));
+            PROF(kKScatter, k_scatter<<<g, kNT, 0, stream>>>(a, wb));
+            int wocc = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc, k_wave, kNT, 0);
+            unsigned wgrid = (unsigned)(std::max(wocc, 1) * cfg.num_sms);
+            void *args[] = {(void *)&head, (void *)&sst, (void *)&a, (void *)&wb};
+            PROF(kKWave, e = cudaLaunchCooperativeKernel((void *)k_wave, wgrid, kNT, args, 0, stream));
+            if (e != cudaSuccess) return e;
+        }
+    }
+    PROF(kKFinalize, k_finalize<<<1, 32, 0, stream>>>(sst, nullptr, a, status_out));
+    return cudaGetLastError();
+}
+
+}  // namespace aceapex

@@ -1,0 +1,50 @@
+// Launch interface between the host API (api.cpp) and the decode kernels (decode.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+
+namespace aceapex {
+
+// Kernel arguments: a single stream travels by value, a batch through a device descriptor array.
+struct LaunchArgs {
+    StreamDesc one;
+    int n_streams;
+    unsigned long long total_tiles;
+    unsigned long long wait_ns;   // limit of every bounded device wait
+    unsigned long long withhold;  // test hook: this tile never publishes its flag (~0 = none)
+};
+
+// Launch shape of the one-pass kernel.
+struct LaunchCfg {
+    int num_sms;
+    int threads;      // 128, 256 or 512
+    int spt;          // sequences per thread per parse chunk
+    int ctas_per_sm;  // 0 = as many as fit
+};
+
+// Device buffers of the wavefront path (carved from the workspace).
+struct WaveBufs {
+    unsigned long long *block_base;  // n_blocks + 1 prefix sums of per-block match counts
+    unsigned long long *mdst, *msrc; // per match: absolute destination and source
+    uint32_t *mlen, *depth, *queue;  // per match: length, depth, level-queue entry
+    uint32_t *gidx;                  // per granule: first match ending after the granule start
+    uint32_t *hist, *lvl, *cursor;   // per level (max_depth + 2 entries)
+};
+
+// Kernel timing (opt-in): CUDA events recorded on the launch stream around each kernel.
+enum KernelId { kKReset = 0, kKFlat, kKFinalize, kKMatchBase, kKParse, kKDepth, kKHist, kKLevels, kKScatter, kKWave,
+                kKCount };
+extern const char *const kKernelNames[kKCount];
+void prof_enable(bool on);
+bool prof_enabled();
+void prof_mark(int id, bool start, cudaStream_t stream);
+int prof_collect(double *ms, unsigned long long *launches);  // kKCount entries each; syncs on the events
+
+cudaError_t launch_flat(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags, const StreamDesc *descs,
+                        const LaunchArgs &a, int32_t *status_out, cudaStream_t stream);
+cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, const LaunchArgs &a, const WaveBufs &wb,
+                        int32_t *status_out, cudaStream_t stream);
+
+}  // namespace aceapex
