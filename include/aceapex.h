@@ -64,6 +64,9 @@ typedef struct {
     uint32_t n_levels;          /* depth levels executed by the wavefront (0 on the one-pass path) */
     uint32_t hist_len;          /* valid entries of level_hist */
     uint64_t level_hist[ACEAPEX_HIST_MAX]; /* level_hist[k] = matches of depth k (k >= 1), clipped */
+    /* with aceapex_profile(1), one-pass path only: SM cycles summed over CTAs spent in each tile phase --
+     * open, parse, literals, store + publish, wait, matches, store -- and [7] = tiles processed */
+    uint64_t phase_cycles[8];
 } aceapex_stats;
 
 /* Host-side header parse.  host_prefix holds at least the first 64 bytes of the stream.
@@ -119,6 +122,17 @@ int aceapex_batch_plan_destroy(aceapex_batch_plan *plan);
 int aceapex_set_launch_config(int threads, int ctas_per_sm, int seqs_per_thread);
 int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *seqs_per_thread);
 
+/* One-pass kernel variant: 0 (default) one warp per tile, used when every tile is at most 4 KiB, else
+ * variant 1; 1 one CTA per tile with a 16 KiB shared-memory image (tiles up to 16 KiB, else variant 2);
+ * 2 one CTA per tile storing bytes straight to HBM (any tile size).  For comparison and testing. */
+int aceapex_set_one_pass_kernel(int kind);
+
+/* Scheduler of streams whose matches are deeper than 1: 1 (default) per-level work queues drained level
+ * by level by one persistent cooperative kernel with a bounded grid barrier between levels; 0 dataflow:
+ * each match is copied by its thread as soon as every match that wrote its source has published its
+ * depth (no level barrier).  Both compute the same per-match depths (§7.1) and the same bytes. */
+int aceapex_set_wave_scheduler(int kind);
+
 /* Decode every stream with the wavefront path, even streams whose max_depth <= 1 would take the one-pass
  * kernel (for testing and comparison).  Applies to later calls on this context. */
 int aceapex_set_force_wavefront(int on);
@@ -144,7 +158,7 @@ int aceapex_get_stats(aceapex_stats *stats);
 const char *aceapex_strerror(int code);
 
 /* ------------------------------------------------------------------------------------------- encoder */
-/* Encoder parameters (host side, CPU).  Defaults: block_log2 20, tile_log2 14, min_match 4,
+/* Encoder parameters (host side, CPU).  Defaults: block_log2 20, tile_log2 12, min_match 4,
  * hash_bits 20, chain_limit 16, flatten 0, depth_cap 0, use_first 1, min_emit 0. */
 typedef struct {
     uint32_t block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit;

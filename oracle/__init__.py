@@ -79,7 +79,7 @@ def _load():
     return _lib
 
 
-def params(block_log2=20, tile_log2=14, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
+def params(block_log2=20, tile_log2=12, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
            depth_cap=0, use_first=1, min_emit=0) -> Params:
     return Params(block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit)
 

@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libaceapex.so")
 _SOURCES = ["decode.cu", "api.cpp", "encoder.cpp"]
-_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh"]
+_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "flat2.cuh", "flat3.cuh", "wave.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 OK, ERR_ARG, ERR_FORMAT, ERR_SIZE, ERR_OFFSET, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_DEPTH = 0, -1, -2, -3, -4, -5, -6, -7, -8
@@ -98,7 +98,7 @@ class Info(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("decoded_len", "comp_len", "n_match", "n_tiles")] + \
                [(n, ctypes.c_uint32) for n in ("max_depth", "one_pass", "n_levels", "hist_len")] + \
-               [("level_hist", ctypes.c_uint64 * HIST_MAX)]
+               [("level_hist", ctypes.c_uint64 * HIST_MAX), ("phase_cycles", ctypes.c_uint64 * 8)]
 
 
 class EncParams(ctypes.Structure):
@@ -111,7 +111,7 @@ class EncParams(ctypes.Structure):
 SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "aceapex_decode_async",
            "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
            "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
-           "aceapex_get_launch_config", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
+           "aceapex_get_launch_config", "aceapex_set_one_pass_kernel", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_encode", "aceapex_free"]
 
@@ -141,6 +141,8 @@ def lib():
             L.aceapex_set_launch_config.argtypes = [i32, i32, i32]
             L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
             L.aceapex_set_force_wavefront.argtypes = [i32]
+            L.aceapex_set_one_pass_kernel.argtypes = [i32]
+            L.aceapex_set_wave_scheduler.argtypes = [i32]
             L.aceapex_set_wait_limit.argtypes = [u64, u64]
             L.aceapex_profile.argtypes = [i32]
             L.aceapex_profile_read.argtypes = [i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -271,6 +273,16 @@ def get_launch_config():
     return t.value, c.value, s.value
 
 
+def set_one_pass_kernel(kind: int) -> None:
+    """0: warp per tile (default, tiles <= 4 KiB); 1: CTA per tile with a 16 KiB image; 2: CTA per tile, direct."""
+    _check(lib().aceapex_set_one_pass_kernel(int(kind)), "aceapex_set_one_pass_kernel")
+
+
+def set_wave_scheduler(kind: int) -> None:
+    """1: per-level queues with a grid barrier per level (default); 0: per-match dataflow."""
+    _check(lib().aceapex_set_wave_scheduler(int(kind)), "aceapex_set_wave_scheduler")
+
+
 def set_force_wavefront(on: bool) -> None:
     lib().aceapex_set_force_wavefront(int(on))
 
@@ -300,10 +312,14 @@ def get_stats() -> dict:
     _check(lib().aceapex_get_stats(ctypes.byref(s)), "aceapex_get_stats")
     return dict(decoded_len=s.decoded_len, comp_len=s.comp_len, n_match=s.n_match, n_tiles=s.n_tiles,
                 max_depth=s.max_depth, one_pass=bool(s.one_pass), n_levels=s.n_levels,
-                level_hist=np.array(s.level_hist[:s.hist_len], dtype=np.uint64))
+                level_hist=np.array(s.level_hist[:s.hist_len], dtype=np.uint64),
+                phase_cycles=dict(zip(PHASE_NAMES, list(s.phase_cycles))))
 
 
-def encode(data, block_log2=20, tile_log2=14, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
+PHASE_NAMES = ["open", "parse", "literals", "store_publish", "wait", "matches", "store", "tiles"]
+
+
+def encode(data, block_log2=20, tile_log2=12, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
            depth_cap=0, use_first=1, min_emit=0) -> np.ndarray:
     """Encode host bytes with the library's CPU encoder; returns the stream as a uint8 numpy array."""
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data)

@@ -58,7 +58,7 @@ constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct WsLayout {
-    size_t head, sst, flags, descs, status, block_base, mdst, msrc, mlen, depth, queue, gidx, hist, lvl, cursor, total;
+    size_t head, sst, flags, descs, status, block_base, mdst, msrc, mlen, depth, queue, gidx, qd, qs, ql, hist, lvl, cursor, total;
 };
 
 // Regions of a workspace.  One-pass: flags per tile.  Wavefront: per-match records, granule index,
@@ -83,6 +83,9 @@ WsLayout layout(int n_streams, uint64_t total_tiles, bool wave, const aceapex_in
         L.depth = at; at = up(at + 4 * nm);
         L.queue = at; at = up(at + 4 * nm);
         L.gidx = at; at = up(at + 4 * ng);
+        L.qd = at; at = up(at + 8 * nm);
+        L.qs = at; at = up(at + 8 * nm);
+        L.ql = at; at = up(at + 4 * nm);
         L.hist = at; at = up(at + 4 * nl);
         L.lvl = at; at = up(at + 4 * (nl + 1));
         L.cursor = at; at = up(at + 4 * nl);
@@ -103,6 +106,9 @@ WaveBufs wave_bufs(uint8_t *ws, const WsLayout &L) {
     w.hist = (uint32_t *)(ws + L.hist);
     w.lvl = (uint32_t *)(ws + L.lvl);
     w.cursor = (uint32_t *)(ws + L.cursor);
+    w.qd = (unsigned long long *)(ws + L.qd);
+    w.qs = (unsigned long long *)(ws + L.qs);
+    w.ql = (uint32_t *)(ws + L.ql);
     return w;
 }
 
@@ -136,7 +142,7 @@ struct DevPool {
 struct Context {
     std::mutex mu;
     std::map<int, DevPool> pools;
-    LaunchCfg cfg{0, 256, 4, 0};
+    LaunchCfg cfg{0, 256, 4, 0, 1, 0};
     bool force_wave = false;
     unsigned long long wait_ns = 4000000000ull;  // bounded device waits give up after 4 s
     unsigned long long withhold = ~0ull;
@@ -195,7 +201,9 @@ int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws,
     a.total_tiles = I.n_tiles;
     a.wait_ns = ctx().wait_ns;
     a.withhold = ctx().withhold;
+    a.max_tile_log2 = I.tile_log2;
     WsHead *head = (WsHead *)(ws + L.head);
+    a.phase = prof_enabled() ? head->phase : nullptr;
     StreamState *sst = (StreamState *)(ws + L.sst);
     cudaError_t e;
     if (use_wave(I)) e = launch_wave(cfg, head, sst, a, wave_bufs(ws, L), status_out, stream);
@@ -257,12 +265,16 @@ int aceapex_decode(const void *comp, size_t comp_len, void *out, size_t out_len,
     const uint32_t nh = std::min<uint32_t>(I.max_depth + 1, ACEAPEX_HIST_MAX);
     if (wave) {
         if (cudaMemcpyAsync(h_hist, p->ws + L.hist, 4 * nh, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-            cudaMemcpyAsync(p->host + 32, p->ws + L.head + offsetof(WsHead, n_levels), 4, cudaMemcpyDeviceToHost,
+            cudaMemcpyAsync(p->host + 32, p->ws + L.head + offsetof(WsHead, depth_seen), 4, cudaMemcpyDeviceToHost,
                             stream) != cudaSuccess)
             return kErrCuda;
     }
+    if (prof_enabled() &&
+        cudaMemcpyAsync(p->host + 32768, p->ws + L.head + offsetof(WsHead, phase), 64, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return kErrCuda;
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (prof_enabled()) memcpy(S.phase_cycles, p->host + 32768, 64);
     if (wave) {
         S.n_levels = *(uint32_t *)(p->host + 32);
         S.hist_len = nh;
@@ -365,6 +377,7 @@ int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *com
             wave_need = std::max(wave_need, layout(1, I.n_tiles, true, &I).total);
         } else {
             P->flat_idx.push_back(i);
+            P->flat_args.max_tile_log2 = std::max(P->flat_args.max_tile_log2, I.tile_log2);
             descs.push_back(make_desc(comps[i], outs[i], I, tiles));
             tiles += I.n_tiles;
         }
@@ -425,10 +438,17 @@ int aceapex_batch_plan_launch(aceapex_batch_plan *P, int graph, void *stream_) {
     std::lock_guard<std::mutex> g(ctx().mu);
     if (!graph) return plan_enqueue(P, stream);
     if (!P->exec) {
-        if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
-        int rc = plan_enqueue(P, stream);
+        // capture on a private stream: the caller's may be the legacy default stream, which cannot capture
+        cudaStream_t cap = nullptr;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(cudaErrorUnknown);
+        }
+        int rc = plan_enqueue(P, cap);
         cudaGraph_t gr = nullptr;
-        cudaError_t e = cudaStreamEndCapture(stream, &gr);
+        cudaError_t e = cudaStreamEndCapture(cap, &gr);
+        cudaStreamDestroy(cap);
         if (rc || e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return rc ? rc : cuda_fail(e); }
         e = cudaGraphInstantiate(&P->exec, gr, 0);
         if (e != cudaSuccess) { cudaGraphDestroy(gr); P->exec = nullptr; return cuda_fail(e); }
@@ -498,6 +518,20 @@ int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *spt) {
     *threads = ctx().cfg.threads;
     *ctas_per_sm = ctx().cfg.ctas_per_sm;
     *spt = ctx().cfg.spt;
+    return kOK;
+}
+
+int aceapex_set_one_pass_kernel(int kind) {
+    if (kind < 0 || kind > 2) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    ctx().cfg.kernel = kind;
+    return kOK;
+}
+
+int aceapex_set_wave_scheduler(int kind) {
+    if (kind < 0 || kind > 1) return kErrArg;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    ctx().cfg.wave_sched = kind;
     return kOK;
 }
 

@@ -22,6 +22,9 @@
 
 #include "decode.h"
 #include "tile.cuh"
+#include "flat2.cuh"
+#include "flat3.cuh"
+#include "wave.cuh"
 
 namespace aceapex {
 
@@ -33,6 +36,7 @@ __global__ void k_reset(WsHead *head, StreamState *sst, const StreamDesc *descs,
         head->epoch = head->epoch + 1 == 0 ? 1 : head->epoch + 1;
         head->ticket = 0; head->ticket2 = 0; head->bar_count = 0; head->bar_gen = 0;
         head->depth_seen = 0; head->n_levels = 0;
+        for (int k = 0; k < 8; k++) head->phase[k] = 0;
     }
     if (i < a.n_streams) {
         const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[i];
@@ -53,14 +57,6 @@ __global__ void k_finalize(StreamState *sst, const StreamDesc *descs, LaunchArgs
     if (status_out) status_out[i] = st.status;
 }
 
-__device__ __forceinline__ int find_stream(const StreamDesc *descs, int n, uint64_t t) {
-    int a = 0, z = n;
-    while (z - a > 1) {
-        const int mid = (a + z) >> 1;
-        if (descs[mid].tile_base <= t) a = mid; else z = mid;
-    }
-    return a;
-}
 
 // ------------------------------------------------------------------------------------------ one-pass kernel
 template <int NT, int SPT>
@@ -236,32 +232,50 @@ __global__ void __launch_bounds__(kNT) k_parse(StreamState *sst, LaunchArgs a, W
 // Depth of every match (§7.1): 1 + the largest depth among the matches that wrote its effective source
 // [s, s + min(L, d - s)); literal bytes count as depth 0.  Chunks of kNT matches are taken in index order;
 // a writer always has a smaller index than its reader, so the lowest unfinished chunk can always finish.
+// One thread copies its match once every writer of its source has published (COPY variant of k_depth):
+// out[d+k] = out[s + (k mod (d-s))], loads through L2, pieces of at most 16 bytes.
+__device__ __forceinline__ void thread_copy(uint8_t *out, uint64_t d, uint64_t s, uint64_t L) {
+    const uint64_t p = d - s;
+    if (p >= L) {
+        for (uint64_t o = 0; o < L; o += 16) lane_copy_out(out, d + o, s + o, (uint32_t)(L - o < 16 ? L - o : 16));
+    } else {
+        uint32_t km = 0;
+        for (uint64_t k = 0; k < L; k++) {
+            out[d + k] = __ldcg(out + s + km);
+            if (++km == (uint32_t)p) km = 0;
+        }
+    }
+}
+
+template <bool COPY>
 __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
     __shared__ unsigned long long s_c;
     __shared__ int s_abort;
+    __shared__ unsigned int s_dmax;
     const StreamDesc &sd = a.one;
     const uint64_t nmatch = sd.n_match;
     const uint32_t gl = sd.tile_log2 < kGranuleLog2 ? sd.tile_log2 : kGranuleLog2;
-    const uint32_t cap = sd.max_depth;
+    const uint32_t cap = sd.max_depth > 0 ? sd.max_depth : 1;
     const uint64_t t0 = global_ns();
+    if (*(volatile int *)&sst[0].status) return;  // the parse failed: the records are not usable
     for (;;) {
-        if (threadIdx.x == 0) { s_c = atomicAdd(&head->ticket2, 1ull); s_abort = 0; }
+        if (threadIdx.x == 0) { s_c = atomicAdd(&head->ticket2, 1ull); s_abort = 0; s_dmax = 0; }
         __syncthreads();
         const uint64_t m = s_c * kNT + threadIdx.x;
         if (s_c * kNT >= nmatch) break;
         bool done = m >= nmatch;
-        uint64_t s = 0, send = 0, w = 0;
+        uint64_t s = 0, send = 0, w = 0, d = 0, L = 0;
         uint32_t mx = 0;
         if (!done) {
-            const uint64_t d = wb.mdst[m];
+            d = wb.mdst[m];
             s = wb.msrc[m];
-            const uint64_t L = wb.mlen[m];
-            if (s < d && d <= sd.N) {  // records are checked by k_parse; stale ones (after an error) read nothing
+            L = wb.mlen[m];
+            if (s < d && d + L <= sd.N) {  // records are checked by k_parse; stale ones (after an error) read nothing
                 send = s + (L < d - s ? L : d - s);
                 w = wb.gidx[s >> gl];
                 while (w < m && wb.mdst[w] + wb.mlen[w] <= s) w++;
             } else {
-                s = send = 0; w = m;
+                s = send = 0; w = m; L = 0;
             }
         }
         int iter = 0;
@@ -269,7 +283,8 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
             if (!done) {
                 // advance over writers whose depth is known; stop at the first unknown one
                 while (w < m && wb.mdst[w] < send) {
-                    const uint32_t dw = ld_relaxed_u32(&wb.depth[w]);
+                    // COPY: a writer's depth is published after its bytes (release/acquire)
+                    const uint32_t dw = COPY ? ld_acquire_u32(&wb.depth[w]) : ld_relaxed_u32(&wb.depth[w]);
                     if (dw == 0) break;
                     mx = dw > mx ? dw : mx;
                     w++;
@@ -277,8 +292,14 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
                 if (!(w < m && wb.mdst[w] < send)) {
                     uint32_t dep = mx + 1;
                     if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
-                    st_relaxed_u32(&wb.depth[m], dep);
-                    atomicMax(&head->depth_seen, dep);
+                    if (COPY) {
+                        if (L) thread_copy(sd.out, d, s, L);
+                        __threadfence();
+                        st_release_u32(&wb.depth[m], dep);
+                    } else {
+                        st_relaxed_u32(&wb.depth[m], dep);
+                    }
+                    atomicMax(&s_dmax, dep);  // one global atomic per chunk (below), not per match
                     done = true;
                 }
             }
@@ -289,6 +310,7 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
             __syncthreads();
             if (s_abort) return;
         }
+        if (threadIdx.x == 0 && s_dmax) atomicMax(&head->depth_seen, s_dmax);
     }
 }
 
@@ -341,33 +363,10 @@ __global__ void __launch_bounds__(kNT) k_scatter(LaunchArgs a, WaveBufs wb) {
     }
 }
 
-// Bounded grid barrier of a cooperative launch.  Returns false when the wait timed out.
-__device__ bool grid_barrier(WsHead *head, StreamState *st, uint64_t t0, uint64_t wait_ns) {
-    __shared__ int s_ok;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        const unsigned gen = ld_acquire_u32(&head->bar_gen);
-        const unsigned arrived = atomicAdd(&head->bar_count, 1u) + 1;
-        if (arrived == gridDim.x) {
-            atomicExch(&head->bar_count, 0u);
-            __threadfence();
-            st_release_u32(&head->bar_gen, gen + 1);
-        } else {
-            while (ld_acquire_u32(&head->bar_gen) == gen) {
-                if (global_ns() - t0 > wait_ns) { report(st, kErrTimeout, kOrderTimeout); s_ok = 0; break; }
-                __nanosleep(32);
-            }
-        }
-    }
-    __syncthreads();
-    return s_ok;
-}
-
 // Drain the per-level queues, level 1 first; one warp copies one match, lanes over 32-byte strides,
 // out[d+k] = out[s + (k mod (d-s))] so that a self-overlapping copy never reads its own output.
 __global__ void __launch_bounds__(kNT) k_wave(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    if (*(volatile int *)&sst[0].status) return;  // uniform: the status is final before this launch
     const uint32_t nlev = head->depth_seen;
     const uint64_t t0 = global_ns();
     const uint32_t lane = threadIdx.x & 31;
@@ -450,15 +449,46 @@ int prof_collect(double *ms, unsigned long long *launches) {
 template <int NT, int SPT>
 static cudaError_t launch_flat_t(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags,
                                  const StreamDesc *descs, const LaunchArgs &a, cudaStream_t stream) {
+    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && cfg.kernel == 0) {
+        // one warp per tile
+        const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;
+        static bool attr3 = false;
+        if (!attr3) {
+            cudaError_t e = cudaFuncSetAttribute(k_flat3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+            attr3 = true;
+        }
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat3, 32 * kWarpsPerCta, dyn);
+        if (e != cudaSuccess) return e;
+        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
+        if (occ < 1) occ = 1;
+        uint64_t grid = (uint64_t)occ * cfg.num_sms;
+        const uint64_t need = (a.total_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        PROF(kKFlat, k_flat3<<<(unsigned)grid, 32 * kWarpsPerCta, dyn, stream>>>(head, sst, flags, descs, a));
+        return cudaGetLastError();
+    }
+    const bool image = a.max_tile_log2 <= (unsigned)kImgLog2 && cfg.kernel != 2;
+    const size_t dyn = image ? sizeof(FlatSmem<NT, SPT>) : 0;
+    static bool attr_set = false;
+    if (image && !attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_flat2<NT, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat<NT, SPT>, NT, 0);
+    cudaError_t e = image ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat2<NT, SPT>, NT, dyn)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat<NT, SPT>, NT, 0);
     if (e != cudaSuccess) return e;
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
     if (occ < 1) occ = 1;
     uint64_t grid = (uint64_t)occ * cfg.num_sms;
     if (grid > a.total_tiles) grid = a.total_tiles;
     if (grid < 1) grid = 1;
-    PROF(kKFlat, k_flat<NT, SPT><<<(unsigned)grid, NT, 0, stream>>>(head, sst, flags, descs, a));
+    if (image) PROF(kKFlat, k_flat2<NT, SPT><<<(unsigned)grid, NT, dyn, stream>>>(head, sst, flags, descs, a));
+    else PROF(kKFlat, k_flat<NT, SPT><<<(unsigned)grid, NT, 0, stream>>>(head, sst, flags, descs, a));
     return cudaGetLastError();
 }
 
@@ -490,23 +520,43 @@ cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, co
     if (sd.N > 0) {
         cudaMemsetAsync(wb.hist, 0, sizeof(uint32_t) * (sd.max_depth + 2), stream);
         PROF(kKMatchBase, k_match_base<<<1, kNT, 0, stream>>>(sst, a, wb.block_base));
-        const uint64_t ptiles = std::min<uint64_t>(sd.n_tiles, (uint64_t)cfg.num_sms * 8);
-        PROF(kKParse, k_parse<<<(unsigned)std::max<uint64_t>(ptiles, 1), kNT, 0, stream>>>(sst, a, wb));
+        if (sd.tile_log2 <= (uint32_t)kWarpImgLog2) {
+            const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;
+            static bool attr = false;
+            if (!attr) {
+                e = cudaFuncSetAttribute(k_parse_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            int pocc = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pocc, k_parse_w, 32 * kWarpsPerCta, dyn);
+            const uint64_t need = (sd.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+            const uint64_t pg = std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)std::max(pocc, 1) * cfg.num_sms));
+            PROF(kKParse, k_parse_w<<<(unsigned)pg, 32 * kWarpsPerCta, dyn, stream>>>(sst, a, wb));
+        } else {
+            const uint64_t ptiles = std::min<uint64_t>(sd.n_tiles, (uint64_t)cfg.num_sms * 8);
+            PROF(kKParse, k_parse<<<(unsigned)std::max<uint64_t>(ptiles, 1), kNT, 0, stream>>>(sst, a, wb));
+        }
         if (sd.n_match > 0) {
             int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_depth, kNT, 0);
+            const bool flow = cfg.wave_sched == 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, flow ? k_depth<true> : k_depth<false>, kNT, 0);
             const uint64_t chunks = (sd.n_match + kNT - 1) / kNT;
             const uint64_t dgrid = std::min<uint64_t>(chunks, (uint64_t)std::max(occ, 1) * cfg.num_sms);
-            PROF(kKDepth, k_depth<<<(unsigned)dgrid, kNT, 0, stream>>>(head, sst, a, wb));
+            if (flow) PROF(kKDepth, k_depth<true><<<(unsigned)dgrid, kNT, 0, stream>>>(head, sst, a, wb));
+            else PROF(kKDepth, k_depth<false><<<(unsigned)dgrid, kNT, 0, stream>>>(head, sst, a, wb));
             const unsigned g = (unsigned)std::min<uint64_t>(chunks, (uint64_t)cfg.num_sms * 4);
             PROF(kKHist, k_hist<<<g, kNT, 0, stream>>>(a, wb));
+            if (flow) {  // matches were copied as their writers published: no level queues needed
+                PROF(kKFinalize, k_finalize<<<1, 32, 0, stream>>>(sst, nullptr, a, status_out));
+                return cudaGetLastError();
+            }
             PROF(kKLevels, k_levels<<<1, kNT, 0, stream>>>(head, a, wb));
-            PROF(kKScatter, k_scatter<<<g, kNT, 0, stream>>>(a, wb));
-            int wocc = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc, k_wave, kNT, 0);
-            unsigned wgrid = (unsigned)(std::max(wocc, 1) * cfg.num_sms);
+            PROF(kKScatter, k_scatter_w<<<g, 256, 0, stream>>>(a, wb));
+            // one 1024-thread CTA per SM: few arrivals per grid barrier
+            unsigned wgrid = (unsigned)cfg.num_sms;
             void *args[] = {(void *)&head, (void *)&sst, (void *)&a, (void *)&wb};
-            PROF(kKWave, e = cudaLaunchCooperativeKernel((void *)k_wave, wgrid, kNT, args, 0, stream));
+            PROF(kKWave, e = cudaLaunchCooperativeKernel((void *)k_wave_w, wgrid, 1024, args, 0, stream));
             if (e != cudaSuccess) return e;
         }
     }

@@ -14,7 +14,10 @@ struct LaunchArgs {
     unsigned long long total_tiles;
     unsigned long long wait_ns;   // limit of every bounded device wait
     unsigned long long withhold;  // test hook: this tile never publishes its flag (~0 = none)
+    unsigned int max_tile_log2;   // largest tile of the launch's streams (selects the image kernel)
+    unsigned long long *phase;    // when profiling: per-phase SM cycles of the one-pass kernel (kPhases)
 };
+constexpr int kPhases = 8;  // open, parse, literals, store+publish, wait, matches, store, tiles
 
 // Launch shape of the one-pass kernel.
 struct LaunchCfg {
@@ -22,6 +25,9 @@ struct LaunchCfg {
     int threads;      // 128, 256 or 512
     int spt;          // sequences per thread per parse chunk
     int ctas_per_sm;  // 0 = as many as fit
+    int wave_sched;   // deep streams: 0 dataflow (each match copied once its writers published), 1 level queues
+    int kernel;       // one-pass kernel: 0 warp per tile (tiles <= 4 KiB) else 1; 1 CTA per tile with a
+                      // 16 KiB image; 2 CTA per tile storing straight to HBM (comparison and testing)
 };
 
 // Device buffers of the wavefront path (carved from the workspace).
@@ -31,6 +37,8 @@ struct WaveBufs {
     uint32_t *mlen, *depth, *queue;  // per match: length, depth, level-queue entry
     uint32_t *gidx;                  // per granule: first match ending after the granule start
     uint32_t *hist, *lvl, *cursor;   // per level (max_depth + 2 entries)
+    unsigned long long *qd, *qs;     // level-ordered match records: destination, source
+    uint32_t *ql;                    //   and length
 };
 
 // Kernel timing (opt-in): CUDA events recorded on the launch stream around each kernel.

@@ -152,4 +152,28 @@ __device__ int64_t block_varints(const uint8_t *sec, uint32_t sec_len, uint32_t 
     return *s_err ? -1 : (int64_t)after;
 }
 
+// Bounded grid barrier of a cooperative launch.  Returns false when the wait timed out.
+__device__ __forceinline__ bool grid_barrier(WsHead *head, StreamState *st, uint64_t t0, uint64_t wait_ns) {
+    __shared__ int s_ok;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        const unsigned gen = ld_acquire_u32(&head->bar_gen);
+        const unsigned arrived = atomicAdd(&head->bar_count, 1u) + 1;
+        if (arrived == gridDim.x) {
+            atomicExch(&head->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&head->bar_gen, gen + 1);
+        } else {
+            while (ld_acquire_u32(&head->bar_gen) == gen) {
+                if (global_ns() - t0 > wait_ns) { report(st, kErrTimeout, kOrderTimeout); s_ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+    }
+    __syncthreads();
+    return s_ok;
+}
+
 }  // namespace aceapex

@@ -49,8 +49,8 @@ struct StreamState {
 };
 
 // Order of an error not tied to a tile: after every tile error, as a sequential decoder would meet it.
-constexpr unsigned long long kOrderTimeout = (1ull << 58) - 4, kOrderTotals = (1ull << 58) - 2,
-                             kOrderDepth = (1ull << 58) - 1;
+constexpr unsigned long long kOrderTotals = (1ull << 58) - 3, kOrderDepth = (1ull << 58) - 2,
+                             kOrderTimeout = (1ull << 58) - 1;
 
 // Head of every workspace.
 struct WsHead {
@@ -61,6 +61,7 @@ struct WsHead {
     unsigned int depth_seen;       // largest computed match depth (wavefront path)
     unsigned int n_levels;
     unsigned int pad[7];
+    unsigned long long phase[8];   // per-phase SM cycles of the one-pass kernel (profiling only)
 };
 
 // Tiles of a stream: every block but the last has 2^(block_log2 - tile_log2) tiles.

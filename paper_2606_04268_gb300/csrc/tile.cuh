@@ -20,7 +20,7 @@ struct TileSmem {
     uint32_t rlen[CH];             // literal-run length
     uint32_t mlen[CH];             // match length (min_match included), 0 for a sequence without match
     uint32_t loff[CH];             // block-relative offset of the literal run in lit[]
-    uint32_t ends[CH];             // varint scratch
+    alignas(16) uint32_t ends[CH]; // varint scratch
     unsigned long long soff[CH];   // absolute match source
     ScanSmem<NT> scan;
     // block and tile context (written by thread 0, read by all)
@@ -180,6 +180,16 @@ __device__ bool chunk_parse(TileSmem<NT, SPT> &sm, bool with_off) {
     }
     __syncthreads();
     return sm.err == 0;
+}
+
+// Stream of global tile t in a batch (descs sorted by tile_base).
+__device__ __forceinline__ int find_stream(const StreamDesc *descs, int n, uint64_t t) {
+    int a = 0, z = n;
+    while (z - a > 1) {
+        const int mid = (a + z) >> 1;
+        if (descs[mid].tile_base <= t) a = mid; else z = mid;
+    }
+    return a;
 }
 
 // Index of the chunk sequence whose output range holds block-relative byte q (start[i] <= q < start[i+1]).

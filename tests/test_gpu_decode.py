@@ -23,12 +23,19 @@ def _lib():
     ax.set_wait_limit(0)
 
 
+def set_path(path: str):
+    """auto: one-pass kernel for depth <= 1, level queues otherwise; wave: level queues for every stream;
+    flow: per-match dataflow for every stream."""
+    ax.set_force_wavefront(path in ("wave", "flow"))
+    ax.set_wave_scheduler(0 if path == "flow" else 1)
+
+
 def check(x: np.ndarray, comp: np.ndarray, path: str = "auto", offset: int = 0):
-    ax.set_force_wavefront(path == "wave")
+    set_path(path)
     try:
         rc, got = gpu_decode(comp, x.size, offset)
     finally:
-        ax.set_force_wavefront(False)
+        set_path("auto")
     assert rc == 0, ax.STATUS_NAMES.get(rc, rc)
     assert first_diff(got, x) is None, first_diff(got, x)
     return got
@@ -41,7 +48,7 @@ def test_small_text_workload_matches_oracle():
     assert oracle.peek(comp).n_blocks == 4
     ref = oracle.decode(comp)
     assert np.array_equal(ref, x)
-    for path in ("auto", "wave"):
+    for path in ("auto", "wave", "flow"):
         got = check(x, comp, path)
         assert np.array_equal(got, ref)
 
@@ -59,8 +66,8 @@ def test_kinds_modes_shapes(kind, mode, shape):
     n = 700_001 if shape[0] >= 16 else 90_001
     x = synth.make(kind, n, hash((kind, mode, shape)) & 0xFFFF)
     comp = oracle.encode(x, block_log2=shape[0], tile_log2=shape[1], **MODES[mode])
-    check(x, comp, "auto")
-    check(x, comp, "wave")
+    for path in ("auto", "wave", "flow"):
+        check(x, comp, path)
 
 
 @pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 4095, 4096, 4097, (1 << 20) - 1, 1 << 20, (1 << 20) + 1,
@@ -93,8 +100,8 @@ def test_self_overlapping_periods(period):
         d = np.cumsum(r + L) - L
         if period > 1:
             assert np.any((L > 0) & (d - s < L)), "expected self-overlapping matches"
-        check(x, comp, "auto")
-        check(x, comp, "wave")
+        for path in ("auto", "wave", "flow"):
+            check(x, comp, path)
 
 
 @pytest.mark.parametrize("offset", list(range(1, 16)))
@@ -105,11 +112,12 @@ def test_unaligned_output(offset):
     check(x, comp, "wave", offset=offset)
 
 
-def test_level_histogram_matches_oracle_depths():
+@pytest.mark.parametrize("path", ["auto", "flow"])
+def test_level_histogram_matches_oracle_depths(path):
     x = synth.make("text", 3 << 20, 77)
     comp = oracle.encode(x)
     dep = oracle.depths(comp)
-    check(x, comp, "auto")
+    check(x, comp, path)
     st = ax.get_stats()
     assert not st["one_pass"] and st["max_depth"] == dep.max()
     hist = np.bincount(dep, minlength=int(dep.max()) + 1)
@@ -153,12 +161,12 @@ def test_malformed_stream_rejected_like_oracle(name):
     c = cases[name]
     rc_o, _ = oracle.decode_rc(c, out_len=x.size)
     assert rc_o != 0
-    for path in ("auto", "wave"):
-        ax.set_force_wavefront(path == "wave")
+    for path in ("auto", "wave", "flow"):
+        set_path(path)
         try:
             rc, _ = gpu_decode(c, x.size)
         finally:
-            ax.set_force_wavefront(False)
+            set_path("auto")
         assert rc != 0, f"{name}/{path}: accepted"
         assert rc == rc_o, f"{name}/{path}: {ax.STATUS_NAMES.get(rc)} vs oracle {oracle.ERR.get(rc_o)}"
 
