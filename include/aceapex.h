@@ -157,6 +157,26 @@ int aceapex_get_stats(aceapex_stats *stats);
 /* Human-readable name of a status code. */
 const char *aceapex_strerror(int code);
 
+/* -------------------------------------------------------------------------------------------- server */
+/*
+ * Continuous-batching decode server.  Requests are device-resident streams (16-byte aligned) with their
+ * header info.  aceapex_server_step admits queued requests in arrival order while stream + output bytes fit
+ * hbm_budget and one of max_slots slots is free (the server allocates each output with the stream-ordered
+ * allocator), then enqueues ONE one-pass launch that advances every admitted request by a slice of its tiles
+ * (each request gets an equal share of tiles_per_step); requests admitted while others are running join the
+ * next launch.  A stream deeper than 1 is decoded whole in the step that admits it.  poll returns 1 once a
+ * request's last launch has completed (with its status and output pointer), 0 while pending; release frees
+ * its output and budget (stream-ordered on `stream`).  step returns the number of queued + running
+ * requests.  One host thread drives a server; the budget counts stream + output bytes.
+ */
+typedef struct aceapex_server aceapex_server;
+int aceapex_server_create(size_t hbm_budget, int max_slots, uint64_t tiles_per_step, aceapex_server **server);
+int64_t aceapex_server_submit(aceapex_server *server, const void *comp, size_t comp_len, const aceapex_info *info);
+int aceapex_server_step(aceapex_server *server, void *stream);
+int aceapex_server_poll(aceapex_server *server, int64_t id, int32_t *status, void **out);
+int aceapex_server_release(aceapex_server *server, int64_t id, void *stream);
+int aceapex_server_destroy(aceapex_server *server);
+
 /* ------------------------------------------------------------------------------------------- encoder */
 /* Encoder parameters (host side, CPU).  Defaults: block_log2 20, tile_log2 12, min_match 4,
  * hash_bits 20, chain_limit 16, flatten 0, depth_cap 0, use_first 1, min_emit 0. */

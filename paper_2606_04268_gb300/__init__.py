@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libaceapex.so")
-_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp"]
+_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp"]
 _HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "flat2.cuh", "flat3.cuh", "wave.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -113,6 +113,8 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
            "aceapex_get_launch_config", "aceapex_set_one_pass_kernel", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
+           "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
+           "aceapex_server_release", "aceapex_server_destroy",
            "aceapex_encode", "aceapex_free"]
 
 _lib = None
@@ -150,6 +152,13 @@ def lib():
             L.aceapex_get_stats.argtypes = [ctypes.POINTER(Stats)]
             L.aceapex_strerror.argtypes = [i32]
             L.aceapex_strerror.restype = ctypes.c_char_p
+            L.aceapex_server_create.argtypes = [sz, i32, u64, ctypes.POINTER(p)]
+            L.aceapex_server_submit.argtypes = [p, p, sz, ctypes.POINTER(Info)]
+            L.aceapex_server_submit.restype = ctypes.c_int64
+            L.aceapex_server_step.argtypes = [p, p]
+            L.aceapex_server_poll.argtypes = [p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(p)]
+            L.aceapex_server_release.argtypes = [p, ctypes.c_int64, p]
+            L.aceapex_server_destroy.argtypes = [p]
             L.aceapex_encode.argtypes = [p, sz, ctypes.POINTER(EncParams), ctypes.POINTER(p)]
             L.aceapex_encode.restype = ctypes.c_int64
             L.aceapex_free.argtypes = [p]
@@ -261,6 +270,77 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching decode server (aceapex_server_*): submit device-resident streams, call step()
+    repeatedly; each step admits what fits the HBM budget and advances every admitted request by a slice of
+    its tiles in one shared launch."""
+
+    def __init__(self, hbm_budget: int = 64 << 30, max_slots: int = 64, tiles_per_step: int = 65536):
+        self._h = ctypes.c_void_p()
+        _check(lib().aceapex_server_create(int(hbm_budget), int(max_slots), int(tiles_per_step), ctypes.byref(self._h)),
+               "aceapex_server_create")
+        self._keep = {}
+
+    def submit(self, comp, info: Info | None = None) -> int:
+        if info is None:
+            info = peek_header(comp[:64].cpu().numpy())
+        rid = lib().aceapex_server_submit(self._h, _dev_ptr(comp), comp.numel(), ctypes.byref(info))
+        if rid < 0:
+            raise AceapexError(int(rid), "aceapex_server_submit")
+        self._keep[rid] = (comp, info)
+        return int(rid)
+
+    def step(self, stream=None) -> int:
+        rc = lib().aceapex_server_step(self._h, _stream_ptr(stream))
+        if rc < 0:
+            raise AceapexError(rc, "aceapex_server_step")
+        return rc
+
+    def poll(self, rid: int):
+        """None while pending, else (status, device pointer of the output)."""
+        st = ctypes.c_int32()
+        ptr = ctypes.c_void_p()
+        rc = lib().aceapex_server_poll(self._h, int(rid), ctypes.byref(st), ctypes.byref(ptr))
+        if rc < 0:
+            raise AceapexError(rc, "aceapex_server_poll")
+        return None if rc == 0 else (int(st.value), ptr.value)
+
+    def output(self, rid: int):
+        """Copy of a finished request's output as a uint8 CUDA tensor."""
+        import torch
+        res = self.poll(rid)
+        assert res is not None, "request not finished"
+        n = int(self._keep[rid][1].decoded_len)
+        out = torch.empty(n, dtype=torch.uint8, device="cuda")
+        if n:
+            out.copy_(_wrap_ptr(res[1], n))
+        return out
+
+    def release(self, rid: int, stream=None) -> None:
+        _check(lib().aceapex_server_release(self._h, int(rid), _stream_ptr(stream)), "aceapex_server_release")
+        self._keep.pop(rid, None)
+
+    def close(self) -> None:
+        if self._h:
+            lib().aceapex_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _wrap_ptr(ptr: int, n: int):
+    """A uint8 CUDA tensor view of n bytes at a raw device pointer (no ownership)."""
+    import torch
+
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (ptr, False), "version": 3}
+    return torch.as_tensor(_Holder(), device="cuda")
 
 
 def set_launch_config(threads: int = 256, ctas_per_sm: int = 0, seqs_per_thread: int = 4) -> None:

@@ -123,6 +123,9 @@ StreamDesc make_desc(const void *comp, void *out, const aceapex_info &I, uint64_
     d.n_match = I.n_match;
     d.tile_base = tile_base;
     d.n_tiles = I.n_tiles;
+    d.tile_off = 0;
+    d.state = nullptr;
+    d.flags = kDescLast;
     d.block_log2 = I.block_log2;
     d.tile_log2 = I.tile_log2;
     d.min_match = I.min_match;
@@ -218,6 +221,38 @@ bool check_ptrs(const void *comp, size_t comp_len, const void *out, size_t out_l
 }
 
 }  // namespace
+
+// Host helpers of the serving engine (serve.cpp).
+namespace aceapex_host {
+LaunchCfg launch_cfg() {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    return ctx().cfg;
+}
+int num_sms() {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    return pool_for_device(&p) ? 1 : p->num_sms;
+}
+// Decode one stream whole into a workspace that the caller keeps (grown on demand).
+int server_enqueue_whole(const void *comp, void *out, const aceapex_info &I, uint8_t **ws, size_t *ws_cap,
+                         int32_t *status_out, cudaStream_t stream) {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    int rc = pool_for_device(&p);
+    if (rc) return rc;
+    const WsLayout L = layout(1, I.n_tiles, use_wave(I), &I);
+    if (L.total > *ws_cap) {
+        cudaStreamSynchronize(stream);
+        cudaFree(*ws);
+        *ws = nullptr;
+        *ws_cap = 0;
+        if (cudaMalloc((void **)ws, L.total) != cudaSuccess) { cudaGetLastError(); *ws = nullptr; return kErrNomem; }
+        if (cudaMemsetAsync(*ws, 0, L.total, stream) != cudaSuccess) return kErrCuda;
+        *ws_cap = L.total;
+    }
+    return enqueue_one(comp, out, I, *ws, L, status_out ? status_out : (int32_t *)(*ws + L.status), p->num_sms, stream);
+}
+}  // namespace aceapex_host
 
 // ================================================================================================ C ABI
 extern "C" {

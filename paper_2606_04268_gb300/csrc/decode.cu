@@ -40,8 +40,12 @@ __global__ void k_reset(WsHead *head, StreamState *sst, const StreamDesc *descs,
     }
     if (i < a.n_streams) {
         const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[i];
-        sst[i].front = sd.tile_base; sst[i].seq_sum = 0; sst[i].match_sum = 0; sst[i].depth_max = 0;
-        sst[i].status = 0; sst[i].err_key = ~0ull;
+        if (sd.state) {
+            sd.state->front = sd.tile_base;  // persistent state: only the launch-local frontier restarts
+        } else {
+            sst[i].front = sd.tile_base; sst[i].seq_sum = 0; sst[i].match_sum = 0; sst[i].depth_max = 0;
+            sst[i].status = 0; sst[i].err_key = ~0ull;
+        }
     }
 }
 
@@ -50,8 +54,9 @@ __global__ void k_finalize(StreamState *sst, const StreamDesc *descs, LaunchArgs
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_streams) return;
     const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[i];
-    StreamState &st = sst[i];
-    if (st.err_key == ~0ull && (st.seq_sum != sd.n_seq || st.match_sum != sd.n_match || st.depth_max != sd.max_depth))
+    StreamState &st = sd.state ? *sd.state : sst[i];
+    if ((sd.flags & kDescLast) && st.err_key == ~0ull &&
+        (st.seq_sum != sd.n_seq || st.match_sum != sd.n_match || st.depth_max != sd.max_depth))
         st.err_key = (kOrderTotals << 4) | (unsigned long long)(-kErrFormat);
     st.status = st.err_key == ~0ull ? 0 : -(int)(st.err_key & 15);
     if (status_out) status_out[i] = st.status;
@@ -76,9 +81,9 @@ __global__ void __launch_bounds__(NT) k_flat(WsHead *head, StreamState *sst, uin
         if (t >= a.total_tiles) break;
         const int si = s_si;
         const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[si];
-        StreamState *st = &sst[si];
+        StreamState *st = sd.state ? sd.state : &sst[si];
         if (threadIdx.x == 0) {
-            const uint64_t lt = t - sd.tile_base;
+            const uint64_t lt = t - sd.tile_base + sd.tile_off;
             const uint32_t sh = sd.block_log2 - sd.tile_log2;
             sm.err = 0; sm.verr = 0;
             // a stream that already failed is skipped (its flags are still published below)
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(NT) k_flat(WsHead *head, StreamState *sst, uin
         __threadfence();
         __syncthreads();
         const int err_a = sm.err;  // negative: a format error of this tile; 1: the stream failed earlier
-        const unsigned long long order = t - sd.tile_base;
+        const unsigned long long order = t - sd.tile_base + sd.tile_off;
         if (threadIdx.x == 0) {
             if (err_a < 0) report(st, err_a, order);
             if (t != a.withhold) st_release_u32(&flags[t], epoch);

@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(NT) k_flat2(WsHead *head, StreamState *sst, ui
         if (t >= a.total_tiles) break;
         const int si = s_si;
         const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[si];
-        StreamState *st = &sst[si];
-        const unsigned long long order = t - sd.tile_base;
+        StreamState *st = sd.state ? sd.state : &sst[si];
+        const unsigned long long order = t - sd.tile_base + sd.tile_off;
         if (threadIdx.x == 0) {
             const uint32_t sh = sd.block_log2 - sd.tile_log2;
             sm.err = 0; sm.verr = 0;

@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) k_flat3(WsHead *head, Strea
             si = __shfl_sync(0xffffffffu, si, 0);
         }
         const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[si];
-        StreamState *st = &sst[si];
-        const unsigned long long order = t - sd.tile_base;
+        StreamState *st = sd.state ? sd.state : &sst[si];
+        const unsigned long long order = t - sd.tile_base + sd.tile_off;
         const uint32_t sh = sd.block_log2 - sd.tile_log2;
         int err = *(volatile int *)&st->status ? 1 : 0;
         err = __shfl_sync(0xffffffffu, err, 0);

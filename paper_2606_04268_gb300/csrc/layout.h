@@ -33,12 +33,17 @@ struct StreamDesc {
     uint64_t n_blocks;
     uint64_t n_seq;       // header totals, checked against the blocks
     uint64_t n_match;
-    uint64_t tile_base;   // global index of this stream's first tile in the launch's tile space
-    uint64_t n_tiles;
+    uint64_t tile_base;   // global index of this launch's first tile of the stream in the launch's tile space
+    uint64_t n_tiles;     // tiles of the stream decoded by this launch
+    uint64_t tile_off;    // index (within the stream) of the first of them: earlier tiles are already decoded
+    struct StreamState *state;  // persistent per-stream state (served requests), else the launch's own array
     uint32_t block_log2, tile_log2, min_match, max_depth;
+    uint32_t flags;       // bit 0: this launch completes the stream: check the header totals at the end
+    uint32_t pad;
 };
+constexpr uint32_t kDescLast = 1;
 
-// Per-stream device state of a launch (zeroed by the reset kernel).
+// Per-stream device state (zeroed by the reset kernel, or once per request by the server).
 struct StreamState {
     unsigned long long front;      // tiles [tile_base, front) are known to have published their literals
     unsigned long long seq_sum;    // sum of the blocks' n_seq
