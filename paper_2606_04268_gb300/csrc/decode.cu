@@ -570,3 +570,16 @@ cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, co
 }
 
 }  // namespace aceapex
+
+// Fresh persistent state of a served request (stream-ordered, no host memory involved).
+namespace aceapex {
+__global__ void k_state_init(StreamState *st) {
+    st->front = 0; st->seq_sum = 0; st->match_sum = 0; st->err_key = ~0ull; st->depth_max = 0; st->status = 0;
+}
+}  // namespace aceapex
+namespace aceapex_host {
+int init_state(aceapex::StreamState *st, cudaStream_t stream) {
+    aceapex::k_state_init<<<1, 1, 0, stream>>>(st);
+    return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+}  // namespace aceapex_host

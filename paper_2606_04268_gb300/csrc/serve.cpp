@@ -27,6 +27,7 @@ int server_enqueue_whole(const void *comp, void *out, const aceapex_info &I, uin
                          int32_t *status_out, cudaStream_t stream);
 LaunchCfg launch_cfg();
 int num_sms();
+int init_state(StreamState *st, cudaStream_t stream);
 }  // namespace aceapex_host
 
 namespace {
@@ -62,7 +63,6 @@ struct aceapex_server {
     size_t ws_stride = 0, flags_cap = 0;
     StreamDesc *h_descs = nullptr;    // pinned, one block per ring entry
     int32_t *h_status = nullptr;      // pinned, one per slot
-    StreamState h_init{};             // template of a fresh state
     cudaEvent_t ev[kMaxStepsInFlight]{};
     long step_no = 0;
     uint8_t *whole_ws = nullptr;      // wavefront workspace for deep streams
@@ -75,7 +75,8 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 bool event_done(aceapex_server *S, long step) {
     if (step < 0) return false;
-    if (step <= S->step_no - kMaxStepsInFlight) return true;  // its ring entry was already waited for
+    // the ring entry of step k is waited for at the start of step k + kMaxStepsInFlight
+    if (step + kMaxStepsInFlight < S->step_no) return true;
     return cudaEventQuery(S->ev[step % kMaxStepsInFlight]) == cudaSuccess;
 }
 
@@ -94,7 +95,6 @@ int aceapex_server_create(size_t hbm_budget, int max_slots, uint64_t tiles_per_s
     S->flags_cap = tiles_per_step + (uint64_t)max_slots;  // slices are rounded up to at least one tile
     S->ws_stride = up256(sizeof(WsHead)) + up256(sizeof(StreamState) * 2) + up256(4 * S->flags_cap) +
                    up256(sizeof(StreamDesc) * (size_t)max_slots) + up256(4 * (size_t)max_slots);
-    S->h_init.err_key = ~0ull;
     bool ok = cudaMalloc((void **)&S->d_state, sizeof(StreamState) * max_slots) == cudaSuccess &&
               cudaMalloc((void **)&S->d_ws, S->ws_stride * kMaxStepsInFlight) == cudaSuccess &&
               cudaMallocHost((void **)&S->h_descs, sizeof(StreamDesc) * max_slots * kMaxStepsInFlight) == cudaSuccess &&
@@ -161,9 +161,7 @@ int aceapex_server_step(aceapex_server *S, void *stream_) {
         r.slot = slot;
         r.phase = 1;
         S->slot_owner[slot] = id;
-        if (cudaMemcpyAsync(&S->d_state[slot], &S->h_init, sizeof(StreamState), cudaMemcpyHostToDevice, stream) !=
-            cudaSuccess)
-            return kErrCuda;
+        if (aceapex_host::init_state(&S->d_state[slot], stream)) return kErrCuda;
         if (r.info.decoded_len == 0) {
             S->h_status[slot] = 0;
             r.phase = 2;
@@ -275,3 +273,4 @@ int aceapex_server_release(aceapex_server *S, int64_t id, void *stream_) {
 }
 
 }  // extern "C"
+
