@@ -95,6 +95,22 @@ int aceapex_decode_async(const void *comp, size_t comp_len, void *out, size_t ou
                          void *d_ws, size_t ws_len, int32_t *d_status, void *stream);
 
 /*
+ * Decode one stream without allocating anything (the paper has no counterpart: this serves callers that
+ * cannot allocate device memory while decoding -- a process whose memory was budgeted up front, real-time
+ * code, or a library that must not use the application's allocator).  Same arguments as
+ * aceapex_decode_async minus the workspace: the scratch is a 1 MiB array in the library's static device
+ * memory, which every GPU that loads the library holds until the process exits.  Only streams whose
+ * matches all have depth <= 1 (chain-flattened), with tiles of at most 4 KiB and at most 261,888 tiles
+ * (about 1 GiB of output at 4 KiB tiles), fit: anything else returns ACEAPEX_ERR_NOMEM at once.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call on a device shares the one array: calls that overlap on the
+ * GPU race and must not be issued (serialise them on one stream).  Enqueued on `stream`, no host
+ * synchronisation; the status goes to *d_status.
+ */
+int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *out, size_t out_len, const aceapex_info *info,
+                           int32_t *d_status, void *stream);
+
+/*
  * Decode n independent streams (blocking).  comps/outs: host arrays of n device pointers; comp_lens and
  * out_lens: host arrays; statuses: host array of n int32 that receives each stream's status.  Streams
  * whose matches all have depth <= 1 are decoded together by one persistent launch over a global tile

@@ -109,6 +109,7 @@ class EncParams(ctypes.Structure):
 
 # every exported symbol of include/aceapex.h
 SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "aceapex_decode_async",
+           "aceapex_decode_noalloc",
            "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
            "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
            "aceapex_get_launch_config", "aceapex_set_one_pass_kernel", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
@@ -135,6 +136,7 @@ def lib():
             L.aceapex_workspace_size.restype = sz
             L.aceapex_decode.argtypes = [p, sz, p, sz, p]
             L.aceapex_decode_async.argtypes = [p, sz, p, sz, ctypes.POINTER(Info), p, sz, p, p]
+            L.aceapex_decode_noalloc.argtypes = [p, sz, p, sz, ctypes.POINTER(Info), p, p]
             L.aceapex_decode_batch.argtypes = [i32, p, p, p, p, p, p]
             L.aceapex_batch_plan_create.argtypes = [i32, p, p, p, p, p, ctypes.POINTER(p)]
             L.aceapex_batch_plan_launch.argtypes = [p, i32, p]
@@ -222,6 +224,16 @@ def decode_async(comp, out, info: Info, workspace, status, stream=None) -> None:
     _check(lib().aceapex_decode_async(_dev_ptr(comp), comp.numel(), _dev_ptr(out) if out.numel() else None,
                                       out.numel(), ctypes.byref(info), _dev_ptr(workspace), workspace.numel(),
                                       status.data_ptr(), _stream_ptr(stream)), "aceapex_decode_async")
+
+
+def decode_noalloc(comp, out, info: Info, status, stream=None) -> None:
+    """Decode without allocating: the library's static device scratch replaces the workspace (see
+    aceapex_decode_noalloc).  For callers that cannot allocate device memory while decoding."""
+    import torch
+    assert status.is_cuda and status.dtype == torch.int32
+    _check(lib().aceapex_decode_noalloc(_dev_ptr(comp), comp.numel(), _dev_ptr(out) if out.numel() else None,
+                                        out.numel(), ctypes.byref(info), status.data_ptr(), _stream_ptr(stream)),
+           "aceapex_decode_noalloc")
 
 
 def _arrays(comps, outs):

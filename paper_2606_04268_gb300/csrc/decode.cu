@@ -583,3 +583,79 @@ int init_state(aceapex::StreamState *st, cudaStream_t stream) {
     return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 }  // namespace aceapex_host
+
+// ================================================================================================ no-alloc entry
+// Some callers cannot allocate device memory at decode time: code running under a memory budget that
+// was fixed up front (a serving process that pre-sized its pools), real-time or embedded callers that
+// forbid allocation on the decode path, or libraries that must not touch the application's allocator.
+// aceapex_decode_noalloc decodes with scratch that exists before any call: a fixed array in the module's
+// static device memory, held by every GPU that loads the library until the process exits.
+#include "../../include/aceapex.h"
+using namespace aceapex;
+namespace {
+
+// Scratch of the one-pass decode: launch head | stream state | status | per-tile flags.
+constexpr size_t kNoAllocBytes = 1u << 20;
+constexpr size_t kNoAllocFlags = 1024;  // byte offset of the flags region
+constexpr uint64_t kNoAllocMaxTiles = (kNoAllocBytes - kNoAllocFlags) / sizeof(uint32_t);
+static_assert(sizeof(WsHead) <= 512 && sizeof(StreamState) <= 256, "no-alloc scratch layout");
+__device__ __align__(256) static uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+// In host code the array's name is only a stand-in: the device address comes from cudaGetSymbolAddress,
+// looked up once per device (with that device current) and kept here.
+constexpr int kMaxDevices = 64;
+void *g_noalloc_addr[kMaxDevices];
+int g_noalloc_sms[kMaxDevices];
+
+}  // namespace
+
+extern "C" int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *out, size_t out_len,
+                                      const aceapex_info *info, int32_t *d_status, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!comp || comp_len < kStreamHeader || ((uintptr_t)comp & 15) || (!out && out_len) || !info || !d_status)
+        return kErrArg;
+    if (info->comp_len != comp_len || info->decoded_len != out_len) return kErrSize;
+    // only the one-pass kernel fits the fixed scratch: streams of depth <= 1, at most kNoAllocMaxTiles tiles
+    // of at most 4 KiB
+    if (info->max_depth > 1 || info->n_tiles > kNoAllocMaxTiles || info->tile_log2 > (uint32_t)kWarpImgLog2)
+        return kErrNomem;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { cudaGetLastError(); return kErrCuda; }
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return kErrCuda; }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return kErrCuda;
+        }
+        g_noalloc_sms[dev] = sms;
+        g_noalloc_addr[dev] = p;
+    }
+    uint8_t *base = (uint8_t *)g_noalloc_addr[dev];
+    WsHead *head = (WsHead *)base;
+    StreamState *sst = (StreamState *)(base + 512);
+    uint32_t *flags = (uint32_t *)(base + kNoAllocFlags);
+    if (info->decoded_len == 0) return cudaMemsetAsync(d_status, 0, 4, stream) == cudaSuccess ? kOK : kErrCuda;
+    LaunchArgs a{};
+    StreamDesc &d = a.one;
+    d.comp = (const uint8_t *)comp; d.out = (uint8_t *)out; d.comp_len = comp_len; d.N = info->decoded_len;
+    d.n_blocks = info->n_blocks; d.n_seq = info->n_seq; d.n_match = info->n_match; d.tile_base = 0;
+    d.n_tiles = info->n_tiles; d.tile_off = 0; d.state = nullptr; d.block_log2 = info->block_log2;
+    d.tile_log2 = info->tile_log2; d.min_match = info->min_match; d.max_depth = info->max_depth; d.flags = kDescLast;
+    a.n_streams = 1;
+    a.total_tiles = info->n_tiles;
+    a.wait_ns = 4000000000ull;
+    a.withhold = ~0ull;
+    a.max_tile_log2 = info->tile_log2;
+    a.phase = nullptr;
+    // k_reset zeroes the launch head and stream state of every call; the tile flags need no clearing:
+    // they hold the epoch of the call that last published them, and each call runs with a new epoch
+    k_reset<<<1, 256, 0, stream>>>(head, sst, nullptr, a);
+    const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;  // below the 48 KiB default: no attribute needed
+    const uint64_t need = (a.total_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)g_noalloc_sms[dev] * 6));
+    k_flat3<<<(unsigned)grid, 32 * kWarpsPerCta, dyn, stream>>>(head, sst, flags, nullptr, a);
+    k_finalize<<<1, 32, 0, stream>>>(sst, nullptr, a, d_status);
+    return cudaGetLastError() == cudaSuccess ? kOK : kErrCuda;
+}
