@@ -42,7 +42,7 @@ WORKLOADS = {
 
 
 def stream_stats(comp: np.ndarray):
-    """Literal and match byte counts from the block headers (FORMAT.md §2.1)."""
+    """Literal and match byte counts from the block headers (stream format §2.1)."""
     hdr = comp[:64].view(np.uint8)
     N = int(hdr[16:24].view(np.uint64)[0])
     nb = int(hdr[24:32].view(np.uint64)[0])

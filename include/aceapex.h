@@ -4,7 +4,7 @@
  * ACEAPEX is an LZ77 format whose back-references are absolute positions in the decoded output and whose
  * output is cut into self-contained blocks of B bytes (paper §3.1); each block carries four arrays:
  * literal bytes, match lengths, absolute offsets and the command sequence of literal-run lengths (§3.2).
- * The byte layout is fixed in FORMAT.md.  Decoding places every sequence with a prefix sum, scatters the
+ * The byte layout is the ACEAPEX stream format, fixed once for this library.  Decoding places every sequence with a prefix sum, scatters the
  * literals and runs the match copies in dependency-depth waves (§7.1); a stream whose matches all read
  * literal bytes (chain flattening, §3.3) decodes in one pass.
  *
@@ -39,7 +39,7 @@ typedef enum {
     ACEAPEX_ERR_DEPTH = -8    /* the stream's max_depth is smaller than the depth of one of its matches */
 } aceapex_status;
 
-/* Header fields of a stream (FORMAT.md §1.1). */
+/* Header fields of a stream (stream format §1.1). */
 typedef struct {
     uint64_t decoded_len;   /* N */
     uint64_t n_blocks;      /* ceil(N / B) */
@@ -70,7 +70,7 @@ typedef struct {
 } aceapex_stats;
 
 /* Host-side header parse.  host_prefix holds at least the first 64 bytes of the stream.
- * Checks magic, version, flags and field ranges (FORMAT.md §1.1). */
+ * Checks magic, version, flags and field ranges (stream format §1.1). */
 int aceapex_peek_header(const void *host_prefix, size_t len, aceapex_info *info);
 
 /* Device workspace bytes needed by aceapex_decode_async for this stream. */

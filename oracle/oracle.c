@@ -8,7 +8,7 @@
  * Contents
  *   oracle_encode     greedy hash-chain encoder with absolute offsets (§3.1), self-contained blocks,
  *                     optional chain flattening (§3.3, global or within-block) and depth cap (§7.4)
- *   oracle_serialize  writes a parse (match list) in the stream format of FORMAT.md
+ *   oracle_serialize  writes a parse (match list) in the ACEAPEX stream format
  *   oracle_decode     the definition of the decoded bytes: blocks in order, sequences in order,
  *                     literal run then byte-by-byte match copy from the absolute source (§3.2)
  *   oracle_parse      lists every sequence (literal-run length, match length, absolute source)
@@ -106,7 +106,7 @@ static uint32_t *parse_depths(uint64_t N, const uint64_t *d, const uint64_t *s, 
 /* ------------------------------------------------------------------------------------------ serializer */
 /*
  * Writes the parse (matches sorted by destination; every other byte is a literal taken from `in`) in the
- * layout of FORMAT.md.  *out is malloc'ed; returns the stream length or a negative error.
+ * layout of the ACEAPEX stream format.  *out is malloc'ed; returns the stream length or a negative error.
  */
 int64_t oracle_serialize(const uint8_t *in, uint64_t N, const uint64_t *d, const uint64_t *s, const uint32_t *L,
                          uint64_t nm, const or_params *prm, uint8_t **out) {
@@ -414,10 +414,10 @@ static int read_block(const uint8_t *c, const or_info *I, uint64_t b, blk_t *k) 
 }
 
 /*
- * Walks every sequence of every block in order.  If `out` is given, performs the decode of FORMAT.md §3:
+ * Walks every sequence of every block in order.  If `out` is given, performs the decode of the stream format (§3 of the format):
  * literal run, then the match byte after byte (so a self-overlapping copy repeats its period).  If
  * `seq_r/seq_L/seq_s/lits` are given, lists the sequences instead (seq_L = 0 when the sequence has no
- * match).  Validates every rule of FORMAT.md, sync table included.
+ * match).  Validates every rule of the stream format, sync table included.
  */
 static int walk(const uint8_t *c, uint64_t comp_len, uint8_t *out, uint64_t out_len, uint64_t *seq_r, uint64_t *seq_L,
                 uint64_t *seq_s, uint8_t *lits, uint64_t cap_seq, uint64_t *n_seq_out) {

@@ -1,4 +1,4 @@
-// Stream layout constants of the ACEAPEX format (FORMAT.md) and the descriptor / workspace structures the
+// Stream layout constants of the ACEAPEX stream format and the descriptor / workspace structures the
 // host code hands to the decode kernels.  Included by host C++ and by CUDA code.
 #pragma once
 #include <stdint.h>
@@ -7,7 +7,7 @@ namespace aceapex {
 
 constexpr uint32_t kMagic = 0x58454341u;  // "ACEX"
 constexpr uint32_t kVersion = 1;
-constexpr uint32_t kStreamHeader = 64;    // stream header bytes (FORMAT.md §1.1)
+constexpr uint32_t kStreamHeader = 64;    // stream header bytes (stream format §1.1)
 constexpr uint32_t kBlockHeader = 32;     // block header bytes (§2.1)
 constexpr uint32_t kSyncEntry = 20;       // sync-table entry bytes (§2.3)
 constexpr uint32_t kMinBlockLog2 = 2, kMaxBlockLog2 = 24;

@@ -1,6 +1,6 @@
 // Tile parsing shared by the one-pass kernel and the wavefront path's parse kernel.
 //
-// A tile is the T-byte slice [j*T, (j+1)*T) of block b's output (FORMAT.md §2.3).  Its sync entry gives the
+// A tile is the T-byte slice [j*T, (j+1)*T) of block b's output (stream format §2.3).  Its sync entry gives the
 // state of the sequence that contains its first byte, so a CTA can parse it with no reference to earlier
 // tiles.  Sequences are handled in chunks of CH = NT*SPT: the CH literal-run lengths (cmd[]) and match
 // lengths (len[]) are decoded block-wide, an exclusive prefix sum places every sequence in the output

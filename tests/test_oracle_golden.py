@@ -1,4 +1,4 @@
-"""The oracle against streams assembled by hand from FORMAT.md, and the worked example of §3.1."""
+"""The oracle against streams assembled by hand in the ACEAPEX stream format, and the worked example of §3.1."""
 import json
 import os
 

@@ -5,7 +5,7 @@
 * brute force: every legal parse of every tiny string decodes to that string (separate file);
 * invariants the paper fixes: sources precede destinations (§3.1), flattened sources are literal bytes
   (§3.3), depth cap honoured (§7.4), header depths equal an independent depth computation (§7.1);
-* malformed streams are rejected with the error of FORMAT.md §5.
+* malformed streams are rejected with the error code the stream format assigns (format §5).
 """
 import numpy as np
 import pytest
