@@ -138,9 +138,11 @@ int aceapex_batch_plan_destroy(aceapex_batch_plan *plan);
 int aceapex_set_launch_config(int threads, int ctas_per_sm, int seqs_per_thread);
 int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *seqs_per_thread);
 
-/* One-pass kernel variant: 0 (default) one warp per tile, used when every tile is at most 4 KiB, else
+/* One-pass kernel variant: 0 one warp per tile, used when every tile is at most 4 KiB, else
  * variant 1; 1 one CTA per tile with a 16 KiB shared-memory image (tiles up to 16 KiB, else variant 2);
- * 2 one CTA per tile storing bytes straight to HBM (any tile size).  For comparison and testing. */
+ * 2 one CTA per tile storing bytes straight to HBM (any tile size); 3 one warp per tile with the tile's
+ * sections staged in shared memory by bulk copies and word-merged copies (tiles up to 4 KiB, else
+ * variant 1); the default is 3.  Returns ACEAPEX_ERR_ARG for another value. */
 int aceapex_set_one_pass_kernel(int kind);
 
 /* Scheduler of streams whose matches are deeper than 1: 1 (default) per-level work queues drained level

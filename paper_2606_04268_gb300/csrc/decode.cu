@@ -24,6 +24,7 @@
 #include "tile.cuh"
 #include "flat2.cuh"
 #include "flat3.cuh"
+#include "flat4.cuh"
 #include "wave.cuh"
 
 namespace aceapex {
@@ -454,7 +455,28 @@ int prof_collect(double *ms, unsigned long long *launches) {
 template <int NT, int SPT>
 static cudaError_t launch_flat_t(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags,
                                  const StreamDesc *descs, const LaunchArgs &a, cudaStream_t stream) {
-    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && cfg.kernel == 0) {
+    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && cfg.kernel == 3) {
+        // one warp per tile, staged sections
+        const size_t dyn = sizeof(F4Warp) * kF4Warps;
+        static bool attr4 = false;
+        if (!attr4) {
+            cudaError_t e = cudaFuncSetAttribute(k_flat4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+            attr4 = true;
+        }
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat4, 32 * kF4Warps, dyn);
+        if (e != cudaSuccess) return e;
+        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
+        if (occ < 1) occ = 1;
+        uint64_t grid = (uint64_t)occ * cfg.num_sms;
+        const uint64_t need = (a.total_tiles + kF4Warps - 1) / kF4Warps;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        PROF(kKFlat, k_flat4<<<(unsigned)grid, 32 * kF4Warps, dyn, stream>>>(head, sst, flags, descs, a));
+        return cudaGetLastError();
+    }
+    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && (cfg.kernel == 0 || cfg.kernel == 3)) {
         // one warp per tile
         const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;
         static bool attr3 = false;

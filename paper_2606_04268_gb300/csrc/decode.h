@@ -27,7 +27,8 @@ struct LaunchCfg {
     int ctas_per_sm;  // 0 = as many as fit
     int wave_sched;   // deep streams: 0 dataflow (each match copied once its writers published), 1 level queues
     int kernel;       // one-pass kernel: 0 warp per tile (tiles <= 4 KiB) else 1; 1 CTA per tile with a
-                      // 16 KiB image; 2 CTA per tile storing straight to HBM (comparison and testing)
+                      // 16 KiB image; 2 CTA per tile storing straight to HBM (comparison and testing);
+                      // 3 warp per tile with staged sections (tiles <= 4 KiB) else 1
 };
 
 // Device buffers of the wavefront path (carved from the workspace).

@@ -24,10 +24,12 @@ def _lib():
 
 
 def set_path(path: str):
-    """auto: one-pass kernel for depth <= 1, level queues otherwise; wave: level queues for every stream;
+    """auto: one-pass kernel (staged warp-per-tile variant) for depth <= 1, level queues otherwise;
+    warp: the same with the unstaged warp-per-tile one-pass variant; wave: level queues for every stream;
     flow: per-match dataflow for every stream."""
     ax.set_force_wavefront(path in ("wave", "flow"))
     ax.set_wave_scheduler(0 if path == "flow" else 1)
+    ax.set_one_pass_kernel(0 if path == "warp" else 3)
 
 
 def check(x: np.ndarray, comp: np.ndarray, path: str = "auto", offset: int = 0):
@@ -66,7 +68,7 @@ def test_kinds_modes_shapes(kind, mode, shape):
     n = 700_001 if shape[0] >= 16 else 90_001
     x = synth.make(kind, n, hash((kind, mode, shape)) & 0xFFFF)
     comp = oracle.encode(x, block_log2=shape[0], tile_log2=shape[1], **MODES[mode])
-    for path in ("auto", "wave", "flow"):
+    for path in ("auto", "warp", "wave", "flow"):
         check(x, comp, path)
 
 
@@ -100,7 +102,7 @@ def test_self_overlapping_periods(period):
         d = np.cumsum(r + L) - L
         if period > 1:
             assert np.any((L > 0) & (d - s < L)), "expected self-overlapping matches"
-        for path in ("auto", "wave", "flow"):
+        for path in ("auto", "warp", "wave", "flow"):
             check(x, comp, path)
 
 
