@@ -1,0 +1,74 @@
+"""Launch-shape autotuner for batched decodes.
+
+The tunable knobs of the one-pass path are the kernel variant (one warp per tile reading the compressed
+sections from global memory, or one warp per tile with the sections staged in shared memory by bulk
+copies), the number of CTAs per SM (occupancy cap of the persistent grid) and, for streams whose tiles
+exceed 4 KiB, the CTA shape of the CTA-per-tile kernel (threads per CTA and sequences per thread per parse
+chunk).  The tuner times every candidate on the caller's plan (CUDA events, plain launches) and keeps the
+fastest; results are cached in a JSON file keyed by the device and a signature of the batch, so a serving
+process tunes once per batch shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import BatchPlan, set_launch_config, set_one_pass_kernel
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
+
+# (one-pass kernel variant, threads, ctas per SM, sequences per thread)
+CANDIDATES = [(k, t, c, s) for k in (3, 0) for c in (0, 4, 3, 2) for (t, s) in ((256, 4),)] + \
+             [(3, t, 0, s) for (t, s) in ((128, 4), (256, 2), (256, 8), (512, 2))]
+
+
+def _key(device_name: str, sms: int, signature: str) -> str:
+    return f"{device_name}|{sms}|{signature}"
+
+
+def apply(cfg) -> None:
+    kernel, threads, ctas, spt = cfg
+    set_one_pass_kernel(kernel)
+    set_launch_config(threads, ctas, spt)
+
+
+def tune(plan: BatchPlan, signature: str, reps: int = 3, cache_path: str = DEFAULT_CACHE, candidates=None,
+         force: bool = False):
+    """Pick the fastest launch configuration for `plan`; applies it and returns (cfg, {cfg: ms})."""
+    import torch
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    key = _key(dev.name, dev.multi_processor_count, signature)
+    cache = {}
+    if os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if not force and key in cache:
+        cfg = tuple(cache[key]["cfg"])
+        apply(cfg)
+        return cfg, {tuple(k): v for k, v in cache[key].get("ms", [])}
+    times = {}
+    stream = torch.cuda.current_stream()
+    for cfg in candidates or CANDIDATES:
+        apply(cfg)
+        plan.launch(stream=stream)  # warm-up (first use of the shape)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.launch(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times[cfg] = e0.elapsed_time(e1) / reps
+    best = min(times, key=times.get)
+    apply(best)
+    cache[key] = {"cfg": list(best), "ms": [[list(k), v] for k, v in times.items()]}
+    try:
+        tmp = cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    except OSError:
+        pass
+    return best, times
