@@ -3,7 +3,9 @@
 A step is one complete decode of one stream (parse, prefix sum, literal scatter, match copies in depth
 waves) of the workload, with the compressed stream already in HBM.  Default workload: 1 GiB of synthetic
 English-like text encoded with full-depth, unflattened chains (the 1 GiB text configuration).  Other
-workloads: --workload fastq-flat | fastq-cap4 (1 GiB FASTQ, chain-flattened / depth cap 4), small (4 MiB).
+workloads: --workload fastq-flat | fastq-cap4 (1 GiB FASTQ, chain-flattened / depth cap 4), text-flat
+(the 1 GiB text, chain-flattened), small (4 MiB), batch (4096 streams, one graph-replayed launch), serve
+(Poisson arrivals into the continuous-batching server against one-at-a-time plain decode).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload text] [--impl ours|reference]
 
@@ -37,6 +39,8 @@ WORKLOADS = {
                    "1 GiB synthetic FASTQ (150-base reads, 64 x 1 Mb references, Q30 Gaussian qualities), "
                    "chain-flattened (global)"),
     "fastq-cap4": ("fastq", GiB, dict(depth_cap=4, min_emit=6), "1 GiB synthetic FASTQ, depth cap 4"),
+    "text-flat": ("text", GiB, dict(flatten=2, min_emit=6),
+                  "1 GiB synthetic English-like text (Zipf s=1.0, 200k words), chain-flattened (global)"),
     "small": ("markov", 4 * MiB, dict(min_match=4), "4 MiB Markov text, 4 blocks, min match 4, unflattened"),
     # multi-stream workloads (run_batch / run_serve)
     "batch": (None, 0, dict(flatten=2, min_emit=6),
@@ -71,6 +75,7 @@ def kernel_bytes(name: str, st: dict) -> float:
         "k_parse": C + L + 24 * nm + N / 16,          # stream, literals, 24 B records, granule index
         "k_depth": 40 * nm,                           # records + writer lookups + depth
         "k_wave": 2 * M + 24 * nm,                    # sources, destinations, queue + records
+        "k_flow": 2 * M + 28 * nm,                    # sources, destinations, records + granule index, depth
         "k_scatter": 8 * nm, "k_hist": 4 * nm,
     }.get(name, 0.0)
 
@@ -136,16 +141,62 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def make_stream(args, rank: int):
+CACHE_DIR = os.environ.get("ACEAPEX_STREAM_CACHE", os.path.join("/tmp", "aceapex_stream_cache"))
+
+
+def _source_tag() -> str:
+    """Hash of the encoder and generator sources: a cached stream is reused only by the same code."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in ("paper_2606_04268_gb300/csrc/encoder.cpp", "synth/gen.c", "synth/__init__.py"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def cached_stream(kind: str, n: int, seed: int, enc: dict):
+    """(input bytes, encoded stream, encode seconds): the stream comes from a file cache when the same code
+    encoded it before on this machine (bench and tests share it), else it is encoded and stored."""
     import paper_2606_04268_gb300 as ax
+    x = synth.make(kind, n, seed)
+    key = "_".join([kind, str(n), str(seed)] + [f"{k}{v}" for k, v in sorted(enc.items())] + [_source_tag()])
+    path = os.path.join(CACHE_DIR, key + ".npy")
+    if os.path.exists(path):
+        comp = np.load(path)
+        if comp.size >= 64 and ax.peek_header(comp[:64]).decoded_len == n:
+            return x, comp, 0.0
+    t0 = time.time()
+    comp = ax.encode(x, **enc)
+    secs = time.time() - t0
+    try:
+        os.makedirs(CACHE_DIR, exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp.npy"
+        np.save(tmp, comp)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return x, comp, secs
+
+
+def _warm_cache(spec):
+    kind, n, seed, enc = spec
+    cached_stream(kind, n, seed, enc)
+    return True
+
+
+def warm_stream_cache(specs):
+    """Encode several big streams at once (spawned workers) into the file cache."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
+        pool.map(_warm_cache, specs, chunksize=1)
+
+
+def make_stream(args, rank: int):
     kind, n, enc, desc = WORKLOADS[args.workload]
     if args.size:
         n = args.size
-    seed = {"text": 2000, "fastq": 3000, "markov": 1000}[kind] + rank
-    x = synth.make(kind, n, seed)
-    t0 = time.time()
-    comp = ax.encode(x, **enc)
-    return x, comp, desc, time.time() - t0
+    x, comp, secs = cached_stream(kind, n, stream_seed(kind, rank), enc)
+    return x, comp, desc, secs
 
 
 def _encode_one(spec):
@@ -180,6 +231,53 @@ def cpu_oracle_baseline(comp: np.ndarray, N: int, min_seconds: float):
         reps += 1
         assert rc == 0
     return N * reps / t_total / 1e9, reps, t_total
+
+
+def _oracle_worker(args):
+    path, N = args
+    import oracle
+    comp = np.load(path, mmap_mode="r")
+    t0 = time.perf_counter()
+    rc, _ = oracle.decode_rc(np.ascontiguousarray(comp), N)
+    assert rc == 0
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_all_cores(comp: np.ndarray, N: int):
+    """lzbench -I style: one oracle decode of the stream per host core, all at once (spawned processes);
+    returns (aggregate GB/s, cores, wall seconds) or None when the stream cannot be shared by file."""
+    import multiprocessing as mp
+    import tempfile
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "stream.npy")
+        try:
+            np.save(path, comp)
+        except OSError:
+            return None
+        with mp.get_context("spawn").Pool(cores) as pool:
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, [(path, N)] * cores, chunksize=1)
+            wall = time.perf_counter() - t0
+    return N * cores / wall / 1e9, cores, wall
+
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest value over all ranks (the step time of the slowest replica); x itself when world == 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def stream_seed(kind: str, rank: int) -> int:
+    """Seed of a replica's stream: each rank decodes its own stream of the workload (weak scaling)."""
+    return {"text": 2000, "fastq": 3000, "markov": 1000}[kind] + rank
 
 
 def dist_setup():
@@ -267,6 +365,8 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     ax.build()
+    if args.wave_scheduler is not None:
+        ax.set_wave_scheduler(args.wave_scheduler)
     x, comp, desc, enc_s = make_stream(args, rank)
     st = stream_stats(comp)
     info = ax.peek_header(comp[:64])
@@ -322,10 +422,7 @@ def run_ours(args):
             torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         assert torch.equal(h_out, torch.from_numpy(x))
-    ms_all = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_all, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_all.item())
+    ms = max_over_ranks(ms, world, "cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -343,6 +440,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": desc, "decoded_bytes": st["N"], "comp_bytes": st["C"], "ratio": round(st["C"] / st["N"], 4),
                    "max_depth": st["max_depth"], "n_match": st["n_match"], "path": "one-pass" if st["max_depth"] <= 1 else "wavefront",
+                   "wave_scheduler": args.wave_scheduler,
                    "parallelism": f"replicas x{world}", "l2": "inputs and outputs larger than L2 (no flush needed)",
                    "encode_s": round(enc_s, 1)},
         "decode_roofline_frac": round(decode_frac, 4),
@@ -358,6 +456,12 @@ def run_ours(args):
         v, reps, secs = cpu_oracle_baseline(comp, st["N"], args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"the workload's stream decoded {reps} times ({secs:.1f} s)"}
+        if args.cpu_all_cores:
+            r = cpu_oracle_all_cores(comp, st["N"])
+            if r:
+                line["cpu_baseline_all_cores"] = {
+                    "value": round(r[0], 4), "unit": "GB/s", "cores": r[1], "kind": "oracle",
+                    "sample": f"one decode of the workload's stream per core, all at once ({r[2]:.1f} s wall)"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -484,10 +588,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t1
         assert (plan.statuses(stream) == 0).all()
-    ms_all = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_all, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_all.item())
+    ms = max_over_ranks(ms, world, "cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -589,6 +690,9 @@ def _serve_plain(ax, torch, pool_dev, sizes, arrivals, which, verify=None):
     return lat, last
 
 
+LOADS = (0.3, 0.5, 0.7, 0.9, 1.1, 1.5)  # offered load, as a fraction of one-at-a-time plain capacity
+
+
 def run_serve(args):
     """Poisson arrivals into the continuous-batching server vs one-request-at-a-time plain decode."""
     import torch
@@ -630,7 +734,7 @@ def run_serve(args):
         arr_v, which_v = _serve_schedule(64, n_pool, 1.0 / mean_svc, 8000 + rank)
         _serve_served(ax, torch, pool_dev, infos, sizes, arr_v, which_v, 8192, verify=d_x)
         _serve_plain(ax, torch, pool_dev, sizes, arr_v, which_v, verify=d_x)
-        for load in (0.7, 1.5):
+        for load in LOADS:
             arrivals, which = _serve_schedule(n_req, n_pool, load / mean_svc, 9000 + rank)
             tot = float(sizes[which].sum())
             _serve_plain(ax, torch, pool_dev, sizes, arrivals[:20], which[:20])
@@ -655,7 +759,7 @@ def run_serve(args):
     ms = served["span_ms"] / n_req  # per request
     line = _base_line(args, served["gbs"] * world, ms, WORKLOADS["serve"][3], {
         "pool_payloads": n_pool, "requests_per_run": n_req, "mean_service_ms_alone": round(1e3 * mean_svc, 3),
-        "offered_load_0.7": results[0.7], "offered_load_1.5": results[1.5], "tiles_per_step": best,
+        "by_offered_load": {str(k): v for k, v in results.items()}, "tiles_per_step": best,
         "value_is": "aggregate GB/s of the served run at offered load 1.5 (of one-at-a-time capacity), "
                     "best tiles_per_step",
         "parallelism": f"replicas x{world}", "encode_s": round(enc_s, 1)})
@@ -682,6 +786,10 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="override the workload size (bytes)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-all-cores", action="store_true",
+                    help="also time one oracle decode per host core at once (lzbench -I style)")
+    ap.add_argument("--wave-scheduler", type=int, default=None, choices=[0, 1, 2],
+                    help="scheduler of deep streams (aceapex_set_wave_scheduler); default: the library's")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -145,10 +145,12 @@ int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *seqs_per_thre
  * variant 1); the default is 3.  Returns ACEAPEX_ERR_ARG for another value. */
 int aceapex_set_one_pass_kernel(int kind);
 
-/* Scheduler of streams whose matches are deeper than 1: 1 (default) per-level work queues drained level
- * by level by one persistent cooperative kernel with a bounded grid barrier between levels; 0 dataflow:
- * each match is copied by its thread as soon as every match that wrote its source has published its
- * depth (no level barrier).  Both compute the same per-match depths (§7.1) and the same bytes. */
+/* Scheduler of streams whose matches are deeper than 1: 1 per-level work queues drained level by level
+ * by one persistent cooperative kernel with a bounded grid barrier between levels; 0 dataflow: each
+ * match is copied by its thread as soon as every match that wrote its source has published its depth
+ * (no level barrier); 2 (default) warp-granular dataflow: a warp takes 32 consecutive matches and copies
+ * them in rounds as their writers finish.  All compute the same per-match depths (§7.1) and the same
+ * bytes.  Returns ACEAPEX_ERR_ARG for another value. */
 int aceapex_set_wave_scheduler(int kind);
 
 /* Decode every stream with the wavefront path, even streams whose max_depth <= 1 would take the one-pass

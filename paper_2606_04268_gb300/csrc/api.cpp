@@ -145,7 +145,7 @@ struct DevPool {
 struct Context {
     std::mutex mu;
     std::map<int, DevPool> pools;
-    LaunchCfg cfg{0, 256, 4, 0, 1, 3};
+    LaunchCfg cfg{0, 256, 4, 0, 2, 3};
     bool force_wave = false;
     unsigned long long wait_ns = 4000000000ull;  // bounded device waits give up after 4 s
     unsigned long long withhold = ~0ull;
@@ -564,7 +564,7 @@ int aceapex_set_one_pass_kernel(int kind) {
 }
 
 int aceapex_set_wave_scheduler(int kind) {
-    if (kind < 0 || kind > 1) return kErrArg;
+    if (kind < 0 || kind > 2) return kErrArg;
     std::lock_guard<std::mutex> g(ctx().mu);
     ctx().cfg.wave_sched = kind;
     return kOK;

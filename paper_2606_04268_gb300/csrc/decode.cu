@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
     __shared__ unsigned long long s_c;
     __shared__ int s_abort;
     __shared__ unsigned int s_dmax;
+    __shared__ uint32_t s_dep[kNT];  // depths of this chunk's matches (0 = not known yet)
     const StreamDesc &sd = a.one;
     const uint64_t nmatch = sd.n_match;
     const uint32_t gl = sd.tile_log2 < kGranuleLog2 ? sd.tile_log2 : kGranuleLog2;
@@ -266,8 +267,10 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
     if (*(volatile int *)&sst[0].status) return;  // the parse failed: the records are not usable
     for (;;) {
         if (threadIdx.x == 0) { s_c = atomicAdd(&head->ticket2, 1ull); s_abort = 0; s_dmax = 0; }
+        s_dep[threadIdx.x] = 0;
         __syncthreads();
-        const uint64_t m = s_c * kNT + threadIdx.x;
+        const uint64_t base = s_c * kNT;
+        const uint64_t m = base + threadIdx.x;
         if (s_c * kNT >= nmatch) break;
         bool done = m >= nmatch;
         uint64_t s = 0, send = 0, w = 0, d = 0, L = 0;
@@ -289,8 +292,10 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
             if (!done) {
                 // advance over writers whose depth is known; stop at the first unknown one
                 while (w < m && wb.mdst[w] < send) {
-                    // COPY: a writer's depth is published after its bytes (release/acquire)
-                    const uint32_t dw = COPY ? ld_acquire_u32(&wb.depth[w]) : ld_relaxed_u32(&wb.depth[w]);
+                    // a writer of this chunk: its depth (and, COPY, its bytes) are visible after the CTA barrier
+                    // of the loop; an earlier chunk's writer publishes its depth after its bytes (release/acquire)
+                    const uint32_t dw = w >= base ? *(volatile uint32_t *)&s_dep[w - base]
+                                                  : (COPY ? ld_acquire_u32(&wb.depth[w]) : ld_relaxed_u32(&wb.depth[w]));
                     if (dw == 0) break;
                     mx = dw > mx ? dw : mx;
                     w++;
@@ -305,6 +310,7 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
                     } else {
                         st_relaxed_u32(&wb.depth[m], dep);
                     }
+                    s_dep[threadIdx.x] = dep;
                     atomicMax(&s_dmax, dep);  // one global atomic per chunk (below), not per match
                     done = true;
                 }
@@ -394,7 +400,7 @@ __global__ void __launch_bounds__(kNT) k_wave(WsHead *head, StreamState *sst, La
 
 // ------------------------------------------------------------------------------------------ host side
 const char *const kKernelNames[kKCount] = {"k_reset", "k_flat", "k_finalize", "k_match_base", "k_parse",
-                                           "k_depth", "k_hist", "k_levels", "k_scatter", "k_wave"};
+                                           "k_depth", "k_hist", "k_levels", "k_scatter", "k_wave", "k_flow"};
 namespace {
 struct Prof {
     bool on = false;
@@ -563,6 +569,19 @@ cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, co
         } else {
             const uint64_t ptiles = std::min<uint64_t>(sd.n_tiles, (uint64_t)cfg.num_sms * 8);
             PROF(kKParse, k_parse<<<(unsigned)std::max<uint64_t>(ptiles, 1), kNT, 0, stream>>>(sst, a, wb));
+        }
+        if (sd.n_match > 0 && cfg.wave_sched == 2) {
+            // warp-granular dataflow: copies and depths in one persistent launch, then the level histogram
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flow_w, 32 * kFlowWarps, 0);
+            const uint64_t groups = (sd.n_match + 31) / 32;
+            const uint64_t fgrid = std::min<uint64_t>((groups + kFlowWarps - 1) / kFlowWarps,
+                                                      (uint64_t)std::max(occ, 1) * cfg.num_sms);
+            PROF(kKFlow, k_flow_w<<<(unsigned)fgrid, 32 * kFlowWarps, 0, stream>>>(head, sst, a, wb));
+            const unsigned g = (unsigned)std::min<uint64_t>((sd.n_match + kNT - 1) / kNT, (uint64_t)cfg.num_sms * 4);
+            PROF(kKHist, k_hist<<<g, kNT, 0, stream>>>(a, wb));
+            PROF(kKFinalize, k_finalize<<<1, 32, 0, stream>>>(sst, nullptr, a, status_out));
+            return cudaGetLastError();
         }
         if (sd.n_match > 0) {
             int occ = 0;

@@ -44,7 +44,7 @@ struct WaveBufs {
 
 // Kernel timing (opt-in): CUDA events recorded on the launch stream around each kernel.
 enum KernelId { kKReset = 0, kKFlat, kKFinalize, kKMatchBase, kKParse, kKDepth, kKHist, kKLevels, kKScatter, kKWave,
-                kKCount };
+                kKFlow, kKCount };
 extern const char *const kKernelNames[kKCount];
 void prof_enable(bool on);
 bool prof_enabled();

@@ -162,56 +162,188 @@ __device__ __forceinline__ void lane_copy_out(uint8_t *out, uint64_t d, uint64_t
         if ((uint32_t)j < len) dp[j] = (uint8_t)(rw[j >> 2] >> (8 * (j & 3)));
 }
 
+// Copy the matches of queue entries [beg, end) with warps warp, warp + nwarps, ...: two matches per warp
+// step -- a half-warp copies a match of at most 16 bytes, lane j <- byte j, so the loads and stores of a
+// match coalesce; four steps are issued together (8 matches in flight per warp); longer or self-overlapping
+// matches take the whole warp, out[d+k] = out[s + (k mod (d-s))].
+__device__ __forceinline__ void wave_level(const WaveBufs &wb, uint8_t *out, uint64_t N, uint64_t beg, uint64_t end,
+                                           uint64_t warp, uint64_t nwarps) {
+    const uint32_t lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    constexpr int U = 4;
+    for (uint64_t g = beg + warp * 2 * U; g < end; g += nwarps * 2 * U) {
+        uint64_t d[U], s[U], L[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t i = g + 2 * u + half;
+            d[u] = 0; s[u] = 0; L[u] = 0;
+            if (i < end) {
+                d[u] = wb.qd[i]; s[u] = wb.qs[i]; L[u] = wb.ql[i];
+                if (s[u] >= d[u] || d[u] + L[u] > N) L[u] = 0;  // never true for records k_parse_w checked
+            }
+        }
+        uint32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const bool small = L[u] <= 16 && d[u] - s[u] >= L[u];
+            v[u] = (small && hl < L[u]) ? (uint32_t)__ldcg(out + s[u] + hl) : 0x100u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (v[u] < 0x100u) out[d[u] + hl] = (uint8_t)v[u];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const bool small = L[u] <= 16 && d[u] - s[u] >= L[u];
+            uint32_t todo = __ballot_sync(0xffffffffu, L[u] > 0 && !small && hl == 0);
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint64_t D = __shfl_sync(0xffffffffu, d[u], l), S = __shfl_sync(0xffffffffu, s[u], l);
+                const uint64_t LL = __shfl_sync(0xffffffffu, L[u], l), P = D - S;
+                for (uint64_t j = lane; j < LL; j += 32) out[D + j] = __ldcg(out + S + (j < P ? j : j % P));
+            }
+        }
+    }
+}
+
+// Levels of at most kSmallLevel matches are drained by CTA 0 alone, a run of consecutive ones separated by
+// CTA barriers only; the grid meets again at the next larger level.  Deep streams end in long runs of small
+// levels, where a grid barrier per level would cost more than the level's copies.
+constexpr uint32_t kSmallLevel = 512;
+
 __global__ void __launch_bounds__(1024) k_wave_w(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    __shared__ uint32_t s_run_end;
     if (*(volatile int *)&sst[0].status) return;  // uniform: the status is final before this launch
     const uint32_t nlev = head->depth_seen;
     const uint64_t t0 = global_ns();
-    const uint32_t lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     uint8_t *out = a.one.out;
-    const uint64_t N = a.one.N, nmatch = a.one.n_match;
-    for (uint32_t k = 1; k <= nlev; k++) {
+    const uint64_t N = a.one.N;
+    uint32_t k = 1;
+    while (k <= nlev) {
         const uint32_t beg = wb.lvl[k], end = wb.lvl[k + 1];
-        // two matches per warp step: a half-warp copies a match of at most 16 bytes, lane j <- byte j, so the
-        // loads and stores of a match coalesce; four steps are issued together (8 matches in flight per
-        // warp); longer or self-overlapping matches take the whole warp
-        constexpr int U = 4;
-        for (uint64_t g = beg + warp * 2 * U; g < end; g += nwarps * 2 * U) {
-            uint64_t d[U], s[U], L[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const uint64_t i = g + 2 * u + half;
-                d[u] = 0; s[u] = 0; L[u] = 0;
-                if (i < end) {
-                    d[u] = wb.qd[i]; s[u] = wb.qs[i]; L[u] = wb.ql[i];
-                    if (s[u] >= d[u] || d[u] + L[u] > N) L[u] = 0;  // never true for records k_parse_w checked
+        if (end - beg > kSmallLevel) {
+            wave_level(wb, out, N, beg, end, warp, nwarps);
+            k++;
+        } else {
+            // the run of small levels [k, k2): every CTA finds k2 the same way
+            uint32_t k2 = k;
+            for (;;) {
+                if (threadIdx.x == 0) s_run_end = 0xFFFFFFFFu;
+                __syncthreads();
+                const uint32_t j = k2 + threadIdx.x;
+                if (j <= nlev && wb.lvl[j + 1] - wb.lvl[j] > kSmallLevel) atomicMin(&s_run_end, j);
+                __syncthreads();
+                const uint32_t e = s_run_end;
+                __syncthreads();
+                if (e != 0xFFFFFFFFu) { k2 = e; break; }
+                k2 += blockDim.x;
+                if (k2 > nlev) { k2 = nlev + 1; break; }
+            }
+            if (blockIdx.x == 0) {
+                const uint64_t cw = threadIdx.x >> 5, cn = blockDim.x >> 5;
+                for (uint32_t q = k; q < k2; q++) {
+                    wave_level(wb, out, N, wb.lvl[q], wb.lvl[q + 1], cw, cn);
+                    __syncthreads();
                 }
             }
-            uint32_t v[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const bool small = L[u] <= 16 && d[u] - s[u] >= L[u];
-                v[u] = (small && hl < L[u]) ? (uint32_t)__ldcg(out + s[u] + hl) : 0x100u;
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++)
-                if (v[u] < 0x100u) out[d[u] + hl] = (uint8_t)v[u];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const bool small = L[u] <= 16 && d[u] - s[u] >= L[u];
-                uint32_t todo = __ballot_sync(0xffffffffu, L[u] > 0 && !small && hl == 0);
-                while (todo) {
-                    const int l = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const uint64_t D = __shfl_sync(0xffffffffu, d[u], l), S = __shfl_sync(0xffffffffu, s[u], l);
-                    const uint64_t LL = __shfl_sync(0xffffffffu, L[u], l), P = D - S;
-                    for (uint64_t j = lane; j < LL; j += 32) out[D + j] = __ldcg(out + S + (j < P ? j : j % P));
-                }
+            k = k2;
+        }
+        if (k <= nlev && !grid_barrier(head, &sst[0], t0, a.wait_ns)) return;
+    }
+}
+
+// Match phase as a warp-granular dataflow (§7.1 without level barriers).  A warp takes 32 consecutive matches
+// (a ticket); lane l owns match m = m0 + l.  Its writers -- the matches whose output overlaps its effective
+// source [s, s + min(L, d - s)) -- have smaller indices and are found through the granule index.  In rounds,
+// every lane whose writers have all finished copies its match, out[d+k] = out[s + (k mod (d-s))], and
+// publishes depth = 1 + the writers' largest depth (nonzero: "finished").  Writers in the same 32 are seen
+// through shared memory; earlier ones through their published depth (relaxed load, then an acquire fence
+// before the source bytes are read; a writer fences its bytes before its depth).  The lowest unfinished
+// match only waits on finished ones, so the persistent grid always progresses; waits are bounded.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+constexpr int kFlowWarps = 8;
+__global__ void __launch_bounds__(32 * kFlowWarps) k_flow_w(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    __shared__ uint32_t s_dep[kFlowWarps][32];
+    const StreamDesc &sd = a.one;
+    const uint64_t nmatch = sd.n_match, N = sd.N;
+    if (*(volatile int *)&sst[0].status) return;  // the parse failed: the records are not usable
+    const uint32_t gl = sd.tile_log2 < kGranuleLog2 ? sd.tile_log2 : kGranuleLog2;
+    const uint32_t cap = sd.max_depth > 0 ? sd.max_depth : 1;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    volatile uint32_t *mydep = s_dep[wid];
+    uint8_t *out = sd.out;
+    const uint64_t t0 = global_ns();
+    uint32_t dmax = 0;
+    for (;;) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(&head->ticket2, 1ull);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        const uint64_t m0 = g * 32;
+        if (m0 >= nmatch) break;
+        const uint64_t m = m0 + lane;
+        mydep[lane] = 0;
+        uint64_t d = 0, s = 0, L = 0, send = 0, w = m;
+        bool done = m >= nmatch;
+        if (!done) {
+            d = __ldg(&wb.mdst[m]); s = __ldg(&wb.msrc[m]); L = __ldg(&wb.mlen[m]);
+            if (s < d && d + L <= N) {  // records are checked by the parse; stale ones (after an error) read nothing
+                send = s + (L < d - s ? L : d - s);
+                w = __ldg(&wb.gidx[s >> gl]);
+                while (w < m && __ldg(&wb.mdst[w]) + __ldg(&wb.mlen[w]) <= s) w++;
+            } else {
+                L = 0; w = m;
             }
         }
-        if (k < nlev && !grid_barrier(head, &sst[0], t0, a.wait_ns)) return;
+        __syncwarp();
+        uint32_t mx = 0, spins = 0;
+        while (!__all_sync(0xffffffffu, done)) {
+            bool ready = false;
+            if (!done) {
+                // advance over finished writers; stop at the first unfinished one
+                while (w < m && __ldg(&wb.mdst[w]) < send) {
+                    const uint32_t dw = w >= m0 ? mydep[w - m0] : ld_relaxed_u32(&wb.depth[w]);
+                    if (dw == 0) break;
+                    mx = dw > mx ? dw : mx;
+                    w++;
+                }
+                ready = !(w < m && __ldg(&wb.mdst[w]) < send);
+            }
+            if (__any_sync(0xffffffffu, ready)) {
+                if (ready) {
+                    fence_acq_rel_gpu();
+                    const uint64_t p = d - s;
+                    if (p >= L) {
+                        for (uint64_t o = 0; o < L; o += 16)
+                            lane_copy_out(out, d + o, s + o, (uint32_t)(L - o < 16 ? L - o : 16));
+                    } else {
+                        uint32_t km = 0;
+                        for (uint64_t k = 0; k < L; k++) {
+                            out[d + k] = __ldcg(out + s + km);
+                            if (++km == (uint32_t)p) km = 0;
+                        }
+                    }
+                    __threadfence();
+                    uint32_t dep = mx + 1;
+                    if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
+                    st_relaxed_u32(&wb.depth[m], dep);
+                    mydep[lane] = dep;
+                    dmax = dep > dmax ? dep : dmax;
+                    done = true;
+                }
+                __syncwarp();
+            } else {
+                if ((++spins & 15) == 0 && __any_sync(0xffffffffu, global_ns() - t0 > a.wait_ns)) {
+                    if (lane == 0) report(&sst[0], kErrTimeout, kOrderTimeout);
+                    return;
+                }
+                __nanosleep(64);
+            }
+        }
     }
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    if (lane == 0 && dmax) atomicMax(&head->depth_seen, dmax);
 }
 
 // Level queues by counting: pass 1 counts the levels of a CTA's contiguous range of matches in shared
@@ -226,18 +358,34 @@ __global__ void __launch_bounds__(256) k_scatter_w(LaunchArgs a, WaveBufs wb) {
     const uint64_t m0 = (uint64_t)blockIdx.x * per, m1 = (m0 + per) < n ? m0 + per : n;
     for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
-    for (uint64_t m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
-        const uint32_t d = wb.depth[m];
-        if (d <= maxd && d < (uint32_t)kScatterLevels) atomicAdd(&cnt[d], 1u);
+    // counts and positions are taken once per group of equal levels in a warp (most matches of a range
+    // share a few shallow levels, so per-thread atomics would serialise on the same counters)
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t m0w = m0; m0w < m1; m0w += blockDim.x) {
+        const uint64_t m = m0w + threadIdx.x;
+        const uint32_t d = m < m1 ? wb.depth[m] : 0xFFFFFFFFu;
+        const bool take = d <= maxd && d < (uint32_t)kScatterLevels;
+        const unsigned peers = __match_any_sync(0xffffffffu, take ? d : 0xFFFFFFFFu);
+        if (take && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x)
         if (cnt[i]) cnt[i] = atomicAdd(&wb.cursor[i], cnt[i]);  // base of this CTA's slice
     __syncthreads();
-    for (uint64_t m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
-        const uint32_t d = wb.depth[m];
-        if (d > maxd) continue;
-        const uint32_t pos = d < (uint32_t)kScatterLevels ? atomicAdd(&cnt[d], 1u) : atomicAdd(&wb.cursor[d], 1u);
+    for (uint64_t m0w = m0; m0w < m1; m0w += blockDim.x) {
+        const uint64_t m = m0w + threadIdx.x;
+        const uint32_t d = m < m1 ? wb.depth[m] : 0xFFFFFFFFu;
+        const bool take = d <= maxd;
+        const unsigned peers = __match_any_sync(0xffffffffu, take ? d : 0xFFFFFFFFu);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        uint32_t base = 0;
+        if (take && (int)lane == leader)
+            base = d < (uint32_t)kScatterLevels ? atomicAdd(&cnt[d], (uint32_t)__popc(peers))
+                                                : atomicAdd(&wb.cursor[d], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (!take) continue;
+        const uint32_t pos = base + rank;
         wb.queue[pos] = (uint32_t)m;
         // the record itself, in level order, so that the drain reads it without an index indirection
         wb.qd[pos] = wb.mdst[m];

@@ -24,11 +24,11 @@ def _lib():
 
 
 def set_path(path: str):
-    """auto: one-pass kernel (staged warp-per-tile variant) for depth <= 1, level queues otherwise;
+    """auto: one-pass kernel (staged warp-per-tile variant) for depth <= 1, warp dataflow otherwise;
     warp: the same with the unstaged warp-per-tile one-pass variant; wave: level queues for every stream;
-    flow: per-match dataflow for every stream."""
-    ax.set_force_wavefront(path in ("wave", "flow"))
-    ax.set_wave_scheduler(0 if path == "flow" else 1)
+    flow: per-match dataflow for every stream; wflow: warp dataflow for every stream."""
+    ax.set_force_wavefront(path in ("wave", "flow", "wflow"))
+    ax.set_wave_scheduler({"flow": 0, "wave": 1}.get(path, 2))
     ax.set_one_pass_kernel(0 if path == "warp" else 3)
 
 
@@ -50,7 +50,7 @@ def test_small_text_workload_matches_oracle():
     assert oracle.peek(comp).n_blocks == 4
     ref = oracle.decode(comp)
     assert np.array_equal(ref, x)
-    for path in ("auto", "wave", "flow"):
+    for path in ("auto", "wave", "flow", "wflow"):
         got = check(x, comp, path)
         assert np.array_equal(got, ref)
 
@@ -68,7 +68,7 @@ def test_kinds_modes_shapes(kind, mode, shape):
     n = 700_001 if shape[0] >= 16 else 90_001
     x = synth.make(kind, n, hash((kind, mode, shape)) & 0xFFFF)
     comp = oracle.encode(x, block_log2=shape[0], tile_log2=shape[1], **MODES[mode])
-    for path in ("auto", "warp", "wave", "flow"):
+    for path in ("auto", "warp", "wave", "flow", "wflow"):
         check(x, comp, path)
 
 
@@ -102,7 +102,7 @@ def test_self_overlapping_periods(period):
         d = np.cumsum(r + L) - L
         if period > 1:
             assert np.any((L > 0) & (d - s < L)), "expected self-overlapping matches"
-        for path in ("auto", "warp", "wave", "flow"):
+        for path in ("auto", "warp", "wave", "flow", "wflow"):
             check(x, comp, path)
 
 
@@ -112,9 +112,10 @@ def test_unaligned_output(offset):
     comp = oracle.encode(x, block_log2=12, tile_log2=5, flatten=2)
     check(x, comp, "auto", offset=offset)
     check(x, comp, "wave", offset=offset)
+    check(x, comp, "wflow", offset=offset)
 
 
-@pytest.mark.parametrize("path", ["auto", "flow"])
+@pytest.mark.parametrize("path", ["auto", "wave", "flow", "wflow"])
 def test_level_histogram_matches_oracle_depths(path):
     x = synth.make("text", 3 << 20, 77)
     comp = oracle.encode(x)
@@ -163,7 +164,7 @@ def test_malformed_stream_rejected_like_oracle(name):
     c = cases[name]
     rc_o, _ = oracle.decode_rc(c, out_len=x.size)
     assert rc_o != 0
-    for path in ("auto", "wave", "flow"):
+    for path in ("auto", "warp", "wave", "flow", "wflow"):
         set_path(path)
         try:
             rc, _ = gpu_decode(c, x.size)
