@@ -66,6 +66,12 @@ def stream_stats(comp: np.ndarray):
                 n_blocks=nb)
 
 
+# DRAM bytes (read + write) per decoded byte of the dominant kernel, from one ncu capture of a 256 MiB case
+# of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / 268435456), scaled
+# to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
+MEASURED_TRAFFIC_PER_BYTE = {}
+
+
 def kernel_bytes(name: str, st: dict) -> float:
     """Algorithmic HBM bytes of one launch of each kernel (stream read once, output written once, each
     match-source byte read once, per-match metadata of the wavefront path at its stored width)."""
@@ -445,7 +451,9 @@ def run_ours(args):
                    "encode_s": round(enc_s, 1)},
         "decode_roofline_frac": round(decode_frac, 4),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind},
+                     "frac": round(ach / hbm_peak, 4), "peak_kind": peak_kind,
+                     "traffic": (round(MEASURED_TRAFFIC_PER_BYTE[(args.workload, dom)] * st["N"])
+                                 if (args.workload, dom) in MEASURED_TRAFFIC_PER_BYTE else None)},
         "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in kern.items()},
         "gpu_launches": int(sum(v[1] for v in kern.values()) // args.steps * args.steps),
         "e2e": {"value": round(st["N"] / e2e_s / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": st["C"],

@@ -141,8 +141,9 @@ int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *seqs_per_thre
 /* One-pass kernel variant: 0 one warp per tile, used when every tile is at most 4 KiB, else
  * variant 1; 1 one CTA per tile with a 16 KiB shared-memory image (tiles up to 16 KiB, else variant 2);
  * 2 one CTA per tile storing bytes straight to HBM (any tile size); 3 one warp per tile with the tile's
- * sections staged in shared memory by bulk copies and word-merged copies (tiles up to 4 KiB, else
- * variant 1); the default is 3.  Returns ACEAPEX_ERR_ARG for another value. */
+ * sections staged in shared memory by bulk copies and word-merged copies, 32 sequences per warp step
+ * (tiles up to 4 KiB and streams up to ~4 GiB, else variant 0); 4 the same with 128 sequences per warp
+ * step, four per lane.  The default is 3.  Returns ACEAPEX_ERR_ARG for another value. */
 int aceapex_set_one_pass_kernel(int kind);
 
 /* Scheduler of streams whose matches are deeper than 1: 1 per-level work queues drained level by level

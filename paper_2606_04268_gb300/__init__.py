@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libaceapex.so")
 _SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp"]
-_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "flat2.cuh", "flat3.cuh", "flat4.cuh", "wave.cuh"]
+_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "flat2.cuh", "flat3.cuh", "flat4.cuh", "flat5.cuh", "wave.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 OK, ERR_ARG, ERR_FORMAT, ERR_SIZE, ERR_OFFSET, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_DEPTH = 0, -1, -2, -3, -4, -5, -6, -7, -8

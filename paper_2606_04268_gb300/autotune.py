@@ -1,8 +1,8 @@
 """Launch-shape autotuner for batched decodes.
 
 The tunable knobs of the one-pass path are the kernel variant (one warp per tile reading the compressed
-sections from global memory, or one warp per tile with the sections staged in shared memory by bulk
-copies), the number of CTAs per SM (occupancy cap of the persistent grid) and, for streams whose tiles
+sections from global memory; one warp per tile with the sections staged in shared memory by bulk copies,
+32 or 128 sequences per warp step), the number of CTAs per SM (occupancy cap of the persistent grid) and, for streams whose tiles
 exceed 4 KiB, the CTA shape of the CTA-per-tile kernel (threads per CTA and sequences per thread per parse
 chunk).  The tuner times every candidate on the caller's plan (CUDA events, plain launches) and keeps the
 fastest; results are cached in a JSON file keyed by the device and a signature of the batch, so a serving
@@ -18,7 +18,7 @@ from . import BatchPlan, set_launch_config, set_one_pass_kernel
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
 # (one-pass kernel variant, threads, ctas per SM, sequences per thread)
-CANDIDATES = [(k, t, c, s) for k in (3, 0) for c in (0, 4, 3, 2) for (t, s) in ((256, 4),)] + \
+CANDIDATES = [(k, t, c, s) for k in (3, 4, 0) for c in (0, 4, 3, 2) for (t, s) in ((256, 4),)] + \
              [(3, t, 0, s) for (t, s) in ((128, 4), (256, 2), (256, 8), (512, 2))]
 
 

@@ -205,6 +205,7 @@ int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws,
     a.wait_ns = ctx().wait_ns;
     a.withhold = ctx().withhold;
     a.max_tile_log2 = I.tile_log2;
+    a.max_n = I.decoded_len;
     WsHead *head = (WsHead *)(ws + L.head);
     a.phase = prof_enabled() ? head->phase : nullptr;
     StreamState *sst = (StreamState *)(ws + L.sst);
@@ -413,6 +414,7 @@ int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *com
         } else {
             P->flat_idx.push_back(i);
             P->flat_args.max_tile_log2 = std::max(P->flat_args.max_tile_log2, I.tile_log2);
+            P->flat_args.max_n = std::max<unsigned long long>(P->flat_args.max_n, I.decoded_len);
             descs.push_back(make_desc(comps[i], outs[i], I, tiles));
             tiles += I.n_tiles;
         }
@@ -557,7 +559,7 @@ int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *spt) {
 }
 
 int aceapex_set_one_pass_kernel(int kind) {
-    if (kind < 0 || kind > 3) return kErrArg;
+    if (kind < 0 || kind > 4) return kErrArg;
     std::lock_guard<std::mutex> g(ctx().mu);
     ctx().cfg.kernel = kind;
     return kOK;

@@ -25,6 +25,7 @@
 #include "flat2.cuh"
 #include "flat3.cuh"
 #include "flat4.cuh"
+#include "flat5.cuh"
 #include "wave.cuh"
 
 namespace aceapex {
@@ -461,7 +462,30 @@ int prof_collect(double *ms, unsigned long long *launches) {
 template <int NT, int SPT>
 static cudaError_t launch_flat_t(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags,
                                  const StreamDesc *descs, const LaunchArgs &a, cudaStream_t stream) {
-    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && cfg.kernel == 3) {
+    // the staged kernels keep positions and tile indices in 32 bits
+    const bool narrow = a.max_n > 0 && a.max_n <= kF4MaxN && a.total_tiles < (1ull << 31);
+    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && cfg.kernel == 4 && narrow) {
+        // one warp per tile, staged sections, 128 sequences per warp step
+        const size_t dyn = sizeof(F5Warp) * kF5Warps;
+        static bool attr5 = false;
+        if (!attr5) {
+            cudaError_t e = cudaFuncSetAttribute(k_flat5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+            attr5 = true;
+        }
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat5, 32 * kF5Warps, dyn);
+        if (e != cudaSuccess) return e;
+        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
+        if (occ < 1) occ = 1;
+        uint64_t grid = (uint64_t)occ * cfg.num_sms;
+        const uint64_t need = (a.total_tiles + kF5Warps - 1) / kF5Warps;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        PROF(kKFlat, k_flat5<<<(unsigned)grid, 32 * kF5Warps, dyn, stream>>>(head, sst, flags, descs, a));
+        return cudaGetLastError();
+    }
+    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && (cfg.kernel == 3 || cfg.kernel == 4) && narrow) {
         // one warp per tile, staged sections
         const size_t dyn = sizeof(F4Warp) * kF4Warps;
         static bool attr4 = false;
@@ -482,7 +506,7 @@ static cudaError_t launch_flat_t(const LaunchCfg &cfg, WsHead *head, StreamState
         PROF(kKFlat, k_flat4<<<(unsigned)grid, 32 * kF4Warps, dyn, stream>>>(head, sst, flags, descs, a));
         return cudaGetLastError();
     }
-    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && (cfg.kernel == 0 || cfg.kernel == 3)) {
+    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && (cfg.kernel == 0 || cfg.kernel == 3 || cfg.kernel == 4)) {
         // one warp per tile
         const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;
         static bool attr3 = false;

@@ -15,6 +15,7 @@ struct LaunchArgs {
     unsigned long long wait_ns;   // limit of every bounded device wait
     unsigned long long withhold;  // test hook: this tile never publishes its flag (~0 = none)
     unsigned int max_tile_log2;   // largest tile of the launch's streams (selects the image kernel)
+    unsigned long long max_n;     // largest decoded length of the launch's streams (0 = unknown)
     unsigned long long *phase;    // when profiling: per-phase SM cycles of the one-pass kernel (kPhases)
 };
 constexpr int kPhases = 8;  // open, parse, literals, store+publish, wait, matches, store, tiles
@@ -28,7 +29,8 @@ struct LaunchCfg {
     int wave_sched;   // deep streams: 0 dataflow (each match copied once its writers published), 1 level queues
     int kernel;       // one-pass kernel: 0 warp per tile (tiles <= 4 KiB) else 1; 1 CTA per tile with a
                       // 16 KiB image; 2 CTA per tile storing straight to HBM (comparison and testing);
-                      // 3 warp per tile with staged sections (tiles <= 4 KiB) else 1
+                      // 3 warp per tile with staged sections (tiles <= 4 KiB, streams < ~4 GiB) else 0;
+                      // 4 the same with 128 sequences per warp step
 };
 
 // Device buffers of the wavefront path (carved from the workspace).

@@ -34,6 +34,7 @@ constexpr uint32_t kF4Stage = 6144;                           // staged section 
 constexpr uint32_t kF4Slack = 48;                             // readable bytes after the staged data
 constexpr uint32_t kF4LitCap = (1u << kWarpImgLog2) + 512;    // literal window staged per tile
 constexpr uint32_t kFull = 0xffffffffu;
+constexpr unsigned long long kF4MaxN = 0xFFF00000ull;      // streams up to ~4 GiB: positions fit 32 bits
 
 struct alignas(16) F4Warp {
     WarpTile c;                                               // tile context, varint hand-off
@@ -99,22 +100,27 @@ __device__ __forceinline__ void or_piece_smem(const uint32_t *base, uint32_t *im
     or_window(imgw + (ib >> 2), a, len, s[0], s[1], s[2], s[3], s[4], s[5], 8 * (P & 3u));
 }
 
-// Piece from global memory: loads only the aligned 16-byte blocks (and at most one word of a third) that
-// hold a byte of [src, src + len).  NC: read-only data (the compressed stream); else decoded output of this
+// Piece from global memory: bytes base[off .. off + len).  Loads only the aligned 16-byte blocks (and at
+// most one word of a third) that hold a byte of that range; the address arithmetic is 32-bit relative to
+// base's 16-byte aligned floor.  NC: read-only data (the compressed stream); else decoded output of this
 // launch, read through L2.
 template <bool NC>
-__device__ __forceinline__ void or_piece_glob(uint32_t *imgw, uint32_t ib, const uint8_t *src, uint32_t len) {
+__device__ __forceinline__ void or_piece_glob(uint32_t *imgw, uint32_t ib, const uint8_t *base, uint32_t off,
+                                              uint32_t len) {
     const uint32_t a = ib & 3u;
-    const uintptr_t g = (uintptr_t)src - a, al = g & ~(uintptr_t)15;
-    const uint32_t o = (uint32_t)(g - al);  // window byte i is byte o + i of the blocks at al
-    const uintptr_t s0 = (uintptr_t)src, s1 = s0 + len;
-    const uint4 *p = reinterpret_cast<const uint4 *>(al);
+    const uint32_t ba = (uint32_t)(uintptr_t)base & 15u;
+    const uint8_t *abase = base - ba;
+    const int32_t g = (int32_t)(ba + off) - (int32_t)a;   // window byte 0, relative to abase
+    const int32_t al = g & ~15;
+    const uint32_t o = (uint32_t)(g - al);               // window byte i is byte o + i of the blocks at al
+    const int32_t s0 = (int32_t)(ba + off), s1 = s0 + (int32_t)len;
+    const uint4 *p = reinterpret_cast<const uint4 *>(abase + al);
     uint4 b0 = make_uint4(0, 0, 0, 0), b1 = make_uint4(0, 0, 0, 0);
     uint32_t b2 = 0;
     if (s0 < al + 16) b0 = NC ? __ldg(p) : __ldcg(p);
     if (s1 > al + 16 && s0 < al + 32) b1 = NC ? __ldg(p + 1) : __ldcg(p + 1);
     if (s1 > al + 32) {
-        const uint32_t *q = reinterpret_cast<const uint32_t *>(al + 32);
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(abase + al + 32);
         b2 = NC ? __ldg(q) : __ldcg(q);
     }
     // words w[q .. q + 5] with q = o >> 2 in 0..3, by a two-stage shifter
@@ -212,18 +218,18 @@ __device__ __forceinline__ uint32_t f4_owner(uint32_t ex, uint32_t i) {
 }
 
 // Match bytes [k, k + len) of a match with source s and period p (p >= length: no wrap) into the image.
-__device__ __forceinline__ void f4_match_piece(uint32_t *imgw, uint32_t ib, const uint8_t *out, uint64_t s,
-                                               uint64_t p, uint32_t k, uint32_t len, bool wrap) {
+__device__ __forceinline__ void f4_match_piece(uint32_t *imgw, uint32_t ib, const uint8_t *out, uint32_t s,
+                                               uint32_t p, uint32_t k, uint32_t len, bool wrap) {
     if (!wrap) {
-        or_piece_glob<false>(imgw, ib, out + s + k, len);
+        or_piece_glob<false>(imgw, ib, out, s + k, len);
         return;
     }
-    // byte k reads s + (k mod p): split at the period boundaries (p < 2^24 here: p < match length)
-    const uint32_t pp = (uint32_t)p;
+    // byte k reads s + (k mod p): split at the period boundaries
+    const uint32_t pp = p;
     uint32_t r = k % pp;
     while (len) {
         const uint32_t c = (pp - r) < len ? pp - r : len;
-        or_piece_glob<false>(imgw, ib, out + s + r, c);
+        or_piece_glob<false>(imgw, ib, out, s + r, c);
         ib += c; len -= c;
         r += c; if (r == pp) r = 0;
     }
@@ -392,13 +398,13 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                     const uint32_t first = len < 16 ? len : 16u;
                     if (first) {
                         if (smem_src) or_piece_smem(wbase, imgw, ib, so, first);
-                        else or_piece_glob<true>(imgw, ib, c.lit + src, first);
+                        else or_piece_glob<true>(imgw, ib, c.lit, src, first);
                     }
                     if (__any_sync(kFull, len > 16)) {
                         const uint32_t second = len > 32 ? 16u : (len > 16 ? len - 16 : 0u);
                         if (second) {
                             if (smem_src) or_piece_smem(wbase, imgw, ib + 16, so + 16, second);
-                            else or_piece_glob<true>(imgw, ib + 16, c.lit + src + 16, second);
+                            else or_piece_glob<true>(imgw, ib + 16, c.lit, src + 16, second);
                         }
                     }
                     // pieces from the third on: round-robin over the warp
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                                 const uint32_t off = 16 * (2 + i - o_ex);
                                 const uint32_t pl = (o_len - off) < 16 ? o_len - off : 16u;
                                 if (smem_src) or_piece_smem(wbase, imgw, o_ib + off, o_so + off, pl);
-                                else or_piece_glob<true>(imgw, o_ib + off, c.lit + o_src + off, pl);
+                                else or_piece_glob<true>(imgw, o_ib + off, c.lit, o_src + off, pl);
                             }
                         }
                     }
@@ -431,7 +437,8 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                     const uint32_t d = start + r;  // block-relative destination
                     const uint32_t x0 = d > lo ? d : lo;
                     const uint32_t x1 = (d + L) < hi ? d + L : hi;
-                    uint64_t s = 0;
+                    uint32_t s = 0;
+                    const uint32_t b0 = (uint32_t)c.b0;
                     if (lane < nm) {
                         const uint32_t q = (seq + lane) * c.w;  // field offset in off[]
                         const bool st_ok = q >= slo[2] && q + c.w <= shi[2];
@@ -454,13 +461,14 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                         }
                         uint64_t v = __funnelshift_r(w0, w1, sh8);
                         if (c.w > 4) v |= (uint64_t)__funnelshift_r(w1, w2, sh8) << 32;
-                        s = c.w >= 8 ? v : (v & ((1ull << (8 * c.w)) - 1));
-                        if (s >= c.b0 + d) err = kErrOffset;
+                        const uint64_t s64 = c.w >= 8 ? v : (v & ((1ull << (8 * c.w)) - 1));
+                        if (s64 >= (uint64_t)b0 + d) err = kErrOffset;
+                        s = (uint32_t)s64;
                     }
                     if (__any_sync(kFull, err != 0)) { err = kErrOffset; break; }
                     const uint32_t len = (lane < nm && x1 > x0) ? x1 - x0 : 0u;
-                    const uint64_t p = c.b0 + d - s;           // source period
-                    const bool wrap = p < (uint64_t)L;
+                    const uint32_t p = b0 + d - s;             // source period (valid lanes: s < b0 + d)
+                    const bool wrap = p < L;
                     const uint32_t k0 = x0 - d;                // first match byte inside the tile
                     const uint32_t ib = x0 - lo + ishift;
                     // the stream tiles holding the source bytes this lane reads must have published their
@@ -468,20 +476,21 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                     // before tile_off were decoded by an earlier launch
                     WPHASE(5);
                     {
-                        uint64_t need = ~0ull, need_hi = 0;
+                        uint32_t need = 0xFFFFFFFFu, need_hi = 0;
+                        const uint32_t ord32 = (uint32_t)order, toff = (uint32_t)sd.tile_off;
                         if (len) {
-                            const uint64_t sa = wrap ? s : s + k0, sb = wrap ? c.b0 + d : s + k0 + len;
-                            const uint64_t ua = sa >> sd.tile_log2, ub = (sb - 1) >> sd.tile_log2;
-                            if (ua < order && ub >= sd.tile_off) {
-                                need = ua > sd.tile_off ? ua : sd.tile_off;
-                                need_hi = ub < order ? ub : order - 1;
+                            const uint32_t sa = wrap ? s : s + k0, sb = wrap ? b0 + d : s + k0 + len;
+                            const uint32_t ua = sa >> sd.tile_log2, ub = (sb - 1) >> sd.tile_log2;
+                            if (ua < ord32 && ub >= toff) {
+                                need = ua > toff ? ua : toff;
+                                need_hi = ub < ord32 ? ub : ord32 - 1;
                             }
                         }
                         const uint64_t t0 = global_ns();
                         for (;;) {
                             bool ok = true;
                             while (need <= need_hi) {
-                                if (ld_acquire_u32(&flags[need - sd.tile_off + sd.tile_base]) != epoch) { ok = false; break; }
+                                if (ld_acquire_u32(&flags[need - toff + (uint32_t)sd.tile_base]) != epoch) { ok = false; break; }
                                 need++;
                             }
                             if (__all_sync(kFull, ok)) break;
@@ -510,7 +519,7 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                             const uint32_t k = f4_owner(ex, i);
                             const uint32_t o_ib = __shfl_sync(kFull, ib, k), o_len = __shfl_sync(kFull, len, k);
                             const uint32_t o_k0 = __shfl_sync(kFull, k0, k), o_ex = __shfl_sync(kFull, ex, k);
-                            const uint64_t o_s = __shfl_sync(kFull, s, k), o_p = __shfl_sync(kFull, p, k);
+                            const uint32_t o_s = __shfl_sync(kFull, s, k), o_p = __shfl_sync(kFull, p, k);
                             const bool o_wrap = __shfl_sync(kFull, (uint32_t)wrap, k) != 0;
                             if (i < total) {
                                 const uint32_t off = 16 * (1 + i - o_ex);

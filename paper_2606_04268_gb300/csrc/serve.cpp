@@ -227,6 +227,7 @@ int aceapex_server_step(aceapex_server *S, void *stream_) {
         a.wait_ns = 4000000000ull;
         a.withhold = ~0ull;
         a.max_tile_log2 = max_tl;
+        for (int k = 0; k < nd; k++) a.max_n = std::max<unsigned long long>(a.max_n, hd[k].N);
         if (nd == 1) a.one = hd[0];
         // launch_flat reads descs[] (device) when n_streams > 1, and a.one otherwise
         cudaError_t e = launch_flat(cfg, head, sst, flags, nd > 1 ? dd : nullptr, a, d_out_status, stream);

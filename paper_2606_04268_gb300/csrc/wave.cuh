@@ -264,26 +264,29 @@ __global__ void __launch_bounds__(1024) k_wave_w(WsHead *head, StreamState *sst,
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 constexpr int kFlowWarps = 8;
-__global__ void __launch_bounds__(32 * kFlowWarps) k_flow_w(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
-    __shared__ uint32_t s_dep[kFlowWarps][32];
+constexpr int kFlowWidth = 32;  // lanes of one worker: a worker takes kFlowWidth consecutive matches
+__global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
+    constexpr int G = kFlowWidth;
+    __shared__ uint32_t s_dep[kFlowWarps * 32];
     const StreamDesc &sd = a.one;
     const uint64_t nmatch = sd.n_match, N = sd.N;
     if (*(volatile int *)&sst[0].status) return;  // the parse failed: the records are not usable
     const uint32_t gl = sd.tile_log2 < kGranuleLog2 ? sd.tile_log2 : kGranuleLog2;
     const uint32_t cap = sd.max_depth > 0 ? sd.max_depth : 1;
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    volatile uint32_t *mydep = s_dep[wid];
+    const uint32_t lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
+    const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (G * grp));
+    volatile uint32_t *mydep = s_dep + (threadIdx.x - sub);
     uint8_t *out = sd.out;
     const uint64_t t0 = global_ns();
     uint32_t dmax = 0;
     for (;;) {
         unsigned long long g = 0;
-        if (lane == 0) g = atomicAdd(&head->ticket2, 1ull);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        const uint64_t m0 = g * 32;
+        if (sub == 0) g = atomicAdd(&head->ticket2, 1ull);
+        g = __shfl_sync(mask, g, 0, G);
+        const uint64_t m0 = g * G;
         if (m0 >= nmatch) break;
-        const uint64_t m = m0 + lane;
-        mydep[lane] = 0;
+        const uint64_t m = m0 + sub;
+        mydep[sub] = 0;
         uint64_t d = 0, s = 0, L = 0, send = 0, w = m;
         bool done = m >= nmatch;
         if (!done) {
@@ -296,9 +299,9 @@ __global__ void __launch_bounds__(32 * kFlowWarps) k_flow_w(WsHead *head, Stream
                 L = 0; w = m;
             }
         }
-        __syncwarp();
+        __syncwarp(mask);
         uint32_t mx = 0, spins = 0;
-        while (!__all_sync(0xffffffffu, done)) {
+        while (!__all_sync(mask, done)) {
             bool ready = false;
             if (!done) {
                 // advance over finished writers; stop at the first unfinished one
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(32 * kFlowWarps) k_flow_w(WsHead *head, Stream
                 }
                 ready = !(w < m && __ldg(&wb.mdst[w]) < send);
             }
-            if (__any_sync(0xffffffffu, ready)) {
+            if (__any_sync(mask, ready)) {
                 if (ready) {
                     fence_acq_rel_gpu();
                     const uint64_t p = d - s;
@@ -328,22 +331,22 @@ __global__ void __launch_bounds__(32 * kFlowWarps) k_flow_w(WsHead *head, Stream
                     uint32_t dep = mx + 1;
                     if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
                     st_relaxed_u32(&wb.depth[m], dep);
-                    mydep[lane] = dep;
+                    mydep[sub] = dep;
                     dmax = dep > dmax ? dep : dmax;
                     done = true;
                 }
-                __syncwarp();
+                __syncwarp(mask);
             } else {
-                if ((++spins & 15) == 0 && __any_sync(0xffffffffu, global_ns() - t0 > a.wait_ns)) {
-                    if (lane == 0) report(&sst[0], kErrTimeout, kOrderTimeout);
+                if ((++spins & 15) == 0 && __any_sync(mask, global_ns() - t0 > a.wait_ns)) {
+                    if (sub == 0) report(&sst[0], kErrTimeout, kOrderTimeout);
                     return;
                 }
                 __nanosleep(64);
             }
         }
     }
-    dmax = __reduce_max_sync(0xffffffffu, dmax);
-    if (lane == 0 && dmax) atomicMax(&head->depth_seen, dmax);
+    dmax = __reduce_max_sync(mask, dmax);
+    if (sub == 0 && dmax) atomicMax(&head->depth_seen, dmax);
 }
 
 // Level queues by counting: pass 1 counts the levels of a CTA's contiguous range of matches in shared

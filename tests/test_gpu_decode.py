@@ -25,11 +25,12 @@ def _lib():
 
 def set_path(path: str):
     """auto: one-pass kernel (staged warp-per-tile variant) for depth <= 1, warp dataflow otherwise;
-    warp: the same with the unstaged warp-per-tile one-pass variant; wave: level queues for every stream;
+    warp: the same with the unstaged warp-per-tile one-pass variant; w5: with the 128-sequences-per-step
+    staged variant; wave: level queues for every stream;
     flow: per-match dataflow for every stream; wflow: warp dataflow for every stream."""
     ax.set_force_wavefront(path in ("wave", "flow", "wflow"))
     ax.set_wave_scheduler({"flow": 0, "wave": 1}.get(path, 2))
-    ax.set_one_pass_kernel(0 if path == "warp" else 3)
+    ax.set_one_pass_kernel({"warp": 0, "w5": 4}.get(path, 3))
 
 
 def check(x: np.ndarray, comp: np.ndarray, path: str = "auto", offset: int = 0):
@@ -68,7 +69,7 @@ def test_kinds_modes_shapes(kind, mode, shape):
     n = 700_001 if shape[0] >= 16 else 90_001
     x = synth.make(kind, n, hash((kind, mode, shape)) & 0xFFFF)
     comp = oracle.encode(x, block_log2=shape[0], tile_log2=shape[1], **MODES[mode])
-    for path in ("auto", "warp", "wave", "flow", "wflow"):
+    for path in ("auto", "warp", "w5", "wave", "flow", "wflow"):
         check(x, comp, path)
 
 
@@ -80,6 +81,7 @@ def test_sizes_and_ragged_tails(n, kind):
     for kw in (dict(), dict(flatten=2)):
         comp = oracle.encode(x, **kw)
         check(x, comp, "auto")
+        check(x, comp, "w5")
 
 
 def test_empty_stream():
@@ -102,7 +104,7 @@ def test_self_overlapping_periods(period):
         d = np.cumsum(r + L) - L
         if period > 1:
             assert np.any((L > 0) & (d - s < L)), "expected self-overlapping matches"
-        for path in ("auto", "warp", "wave", "flow", "wflow"):
+        for path in ("auto", "warp", "w5", "wave", "flow", "wflow"):
             check(x, comp, path)
 
 
@@ -113,6 +115,7 @@ def test_unaligned_output(offset):
     check(x, comp, "auto", offset=offset)
     check(x, comp, "wave", offset=offset)
     check(x, comp, "wflow", offset=offset)
+    check(x, comp, "w5", offset=offset)
 
 
 @pytest.mark.parametrize("path", ["auto", "wave", "flow", "wflow"])
@@ -164,7 +167,7 @@ def test_malformed_stream_rejected_like_oracle(name):
     c = cases[name]
     rc_o, _ = oracle.decode_rc(c, out_len=x.size)
     assert rc_o != 0
-    for path in ("auto", "warp", "wave", "flow", "wflow"):
+    for path in ("auto", "warp", "w5", "wave", "flow", "wflow"):
         set_path(path)
         try:
             rc, _ = gpu_decode(c, x.size)
