@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
         __syncwarp();
         // ---------------------------------------------------------------- staging
         // section k: [slo[k], shi[k]) of its offsets is staged at W.stage + soff[k] (slo = ~0 when not staged)
-        uint32_t slo[4], shi[4], soff[4], slen[4];
+        uint32_t slo[4], shi[4], soff[4];
         const uint8_t *sbase[4];
         uint32_t staged = 0;
         if (!err) {
@@ -288,7 +288,6 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
             const uint32_t ch = c.chk_cmd + 32, lh = c.chk_len + 32;
             const uint32_t want_hi[4] = {ch < c.cmd_bytes ? ch : c.cmd_bytes, lh < c.len_bytes ? lh : c.len_bytes,
                                          m_hi * w, bx};
-            slen[0] = c.cmd_bytes; slen[1] = c.len_bytes; slen[2] = c.n_match * w; slen[3] = c.n_lit;
             sbase[0] = c.cmd; sbase[1] = c.len; sbase[2] = c.off; sbase[3] = c.lit;
             uint32_t used = 0;
 #pragma unroll
