@@ -111,6 +111,21 @@ int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *out, size_t 
                            int32_t *d_status, void *stream);
 
 /*
+ * Decode a stream held in HOST memory into a host buffer (blocking; §3.1 blocks, §7.1 decode).
+ * h_comp: comp_len bytes of an ACEAPEX stream in host memory; h_out: out_len = decoded length bytes of host
+ * memory; both are the caller's and are only read / written during the call.  The library copies the
+ * stream to device memory it owns (kept for later calls, grown on demand), decodes, and copies the output
+ * back.  One-pass streams (depth <= 1) are cut into up to 16 slices of whole blocks: a slice's stream
+ * bytes are copied in, its tiles decoded and its output copied out on three CUDA streams, so transfers in
+ * both directions overlap the decode.  Deeper streams are copied, decoded whole, and copied back.  With
+ * pinned (page-locked) buffers the copies are asynchronous; pageable buffers work but serialise.  Work
+ * is ordered after the caller's earlier work on `stream`.  Returns the decode status; ACEAPEX_ERR_ARG for
+ * null pointers, ACEAPEX_ERR_SIZE when the lengths disagree with the header, ACEAPEX_ERR_NOMEM when the
+ * device buffers cannot be allocated.
+ */
+int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t out_len, void *stream);
+
+/*
  * Decode n independent streams (blocking).  comps/outs: host arrays of n device pointers; comp_lens and
  * out_lens: host arrays; statuses: host array of n int32 that receives each stream's status.  Streams
  * whose matches all have depth <= 1 are decoded together by one persistent launch over a global tile

@@ -112,7 +112,7 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_decode_noalloc",
            "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
            "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
-           "aceapex_get_launch_config", "aceapex_set_one_pass_kernel", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
+           "aceapex_decode_host", "aceapex_get_launch_config", "aceapex_set_one_pass_kernel", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
            "aceapex_server_release", "aceapex_server_destroy",
@@ -146,6 +146,7 @@ def lib():
             L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
             L.aceapex_set_force_wavefront.argtypes = [i32]
             L.aceapex_set_one_pass_kernel.argtypes = [i32]
+            L.aceapex_decode_host.argtypes = [p, sz, p, sz, p]
             L.aceapex_set_wave_scheduler.argtypes = [i32]
             L.aceapex_set_wait_limit.argtypes = [u64, u64]
             L.aceapex_profile.argtypes = [i32]
@@ -213,6 +214,28 @@ def decode_status(comp, out, stream=None) -> int:
 
 def decode(comp, out, stream=None):
     _check(decode_status(comp, out, stream), "aceapex_decode")
+    return out
+
+
+def _host_ptr(a) -> tuple[int, int]:
+    """(address, byte length) of a contiguous host numpy array or CPU tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"] and a.dtype == np.uint8
+        return a.ctypes.data, a.size
+    assert not a.is_cuda and a.is_contiguous() and a.element_size() == 1
+    return a.data_ptr(), a.numel()
+
+
+def decode_host_status(comp, out, stream=None) -> int:
+    """Decode a stream in host memory into a host buffer (aceapex_decode_host); returns the status code.
+    comp/out: uint8 numpy arrays or CPU tensors (pinned memory lets the copies overlap the decode)."""
+    cp, cn = _host_ptr(comp)
+    op, on = _host_ptr(out)
+    return lib().aceapex_decode_host(cp, cn, op if on else None, on, _stream_ptr(stream))
+
+
+def decode_host(comp, out, stream=None):
+    _check(decode_host_status(comp, out, stream), "aceapex_decode_host")
     return out
 
 

@@ -134,12 +134,21 @@ StreamDesc make_desc(const void *comp, void *out, const aceapex_info &I, uint64_
 }
 
 // ------------------------------------------------------------------------------------------ context
+constexpr int kHostSlices = 16;  // most slices of one overlapped host-buffer decode
+
 struct DevPool {
     uint8_t *ws = nullptr;
     size_t cap = 0;
     uint8_t *host = nullptr;  // pinned: header read-back, status, level histogram
     size_t host_cap = 0;
     int num_sms = 0;
+    // host-buffer decodes: device copies of the stream and the output, one persistent stream state, and the
+    // copy-in / copy-out streams and events of the overlap
+    uint8_t *hd_comp = nullptr, *hd_out = nullptr;
+    size_t hd_comp_cap = 0, hd_out_cap = 0;
+    StreamState *hd_state = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[kHostSlices]{}, ev_dec[kHostSlices]{};
 };
 
 struct Context {
@@ -223,8 +232,9 @@ bool check_ptrs(const void *comp, size_t comp_len, const void *out, size_t out_l
 
 }  // namespace
 
-// Host helpers of the serving engine (serve.cpp).
+// Host helpers of the serving engine (serve.cpp); init_state is defined with the kernels (decode.cu).
 namespace aceapex_host {
+int init_state(aceapex::StreamState *st, cudaStream_t stream);
 LaunchCfg launch_cfg() {
     std::lock_guard<std::mutex> g(ctx().mu);
     return ctx().cfg;
@@ -607,6 +617,132 @@ int aceapex_get_stats(aceapex_stats *s) {
     std::lock_guard<std::mutex> g(ctx().mu);
     *s = ctx().stats;
     return kOK;
+}
+
+// ------------------------------------------------------------------------------------------ host buffers
+namespace {
+int grow(uint8_t **buf, size_t *cap, size_t need) {
+    if (need <= *cap) return kOK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void **)buf, need) != cudaSuccess) { cudaGetLastError(); *buf = nullptr; return kErrNomem; }
+    *cap = need;
+    return kOK;
+}
+int host_path_init(DevPool &p) {
+    if (p.s_in) return kOK;
+    bool ok = cudaStreamCreateWithFlags(&p.s_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.s_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc((void **)&p.hd_state, sizeof(StreamState)) == cudaSuccess;
+    for (int k = 0; ok && k < kHostSlices; k++)
+        ok = cudaEventCreateWithFlags(&p.ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.ev_dec[k], cudaEventDisableTiming) == cudaSuccess;
+    return ok ? kOK : cuda_fail(cudaErrorUnknown);
+}
+}  // namespace
+
+int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t out_len, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!h_comp || comp_len < kStreamHeader || (!h_out && out_len)) return kErrArg;
+    aceapex_info I;
+    int rc = parse_header((const uint8_t *)h_comp, kStreamHeader, &I);
+    if (rc) return rc;
+    if (I.comp_len != comp_len || I.decoded_len != out_len) return kErrSize;
+    if (I.decoded_len == 0) return (I.n_blocks || I.n_match || I.n_seq || I.max_depth) ? kErrFormat : kOK;
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    rc = pool_for_device(&p);
+    if (!rc) rc = host_path_init(*p);
+    if (!rc) rc = grow(&p->hd_comp, &p->hd_comp_cap, comp_len);
+    if (!rc) rc = grow(&p->hd_out, &p->hd_out_cap, out_len);
+    if (rc) return rc;
+    const bool wave = use_wave(I);
+    const WsLayout L = layout(1, I.n_tiles, wave, &I);
+    rc = pool_reserve(*p, L.total, stream);
+    if (rc) return rc;
+    aceapex_stats &S = ctx().stats;
+    memset(&S, 0, sizeof(S));
+    S.decoded_len = I.decoded_len; S.comp_len = I.comp_len; S.n_match = I.n_match; S.n_tiles = I.n_tiles;
+    S.max_depth = I.max_depth;
+    S.one_pass = !wave;
+    const uint8_t *hc = (const uint8_t *)h_comp;
+    uint8_t *ho = (uint8_t *)h_out;
+    int32_t *d_status = (int32_t *)(p->ws + L.status);
+    int32_t *h_status = (int32_t *)p->host;
+    // slices: whole blocks of the stream in order; a slice's stream bytes end where its last block ends
+    const uint64_t B = 1ull << I.block_log2, T = 1ull << I.tile_log2, tpb = B / T;
+    int ns = (int)std::min<uint64_t>((uint64_t)kHostSlices, (I.decoded_len + (32ull << 20) - 1) / (32ull << 20));
+    if (ns < 1) ns = 1;
+    if (wave || I.n_blocks < (uint64_t)ns) ns = 1;
+    // the block index must be usable to cut the stream; otherwise copy it whole (the kernels report the error)
+    std::vector<uint64_t> cut(ns + 1, 0);
+    uint64_t t_beg[kHostSlices + 1];
+    for (int k = 0; k <= ns; k++) {
+        const uint64_t bb = (I.n_blocks * (uint64_t)k) / (uint64_t)ns;  // first block of slice k
+        t_beg[k] = k == ns ? I.n_tiles : bb * tpb;
+        if (k == ns || k == 0) { cut[k] = k == ns ? comp_len : 0; continue; }
+        cut[k] = rd(hc + kStreamHeader + 8 * bb, 8);
+    }
+    for (int k = 1; k <= ns; k++)
+        if (cut[k] < cut[k - 1] || cut[k] > comp_len || (cut[k] & 15)) { ns = 1; cut[1] = comp_len; t_beg[1] = I.n_tiles; break; }
+    // every copy and launch below waits for the caller's earlier work on its stream
+    if (cudaEventRecord(p->ev_dec[0], stream) != cudaSuccess || cudaStreamWaitEvent(p->s_in, p->ev_dec[0], 0) != cudaSuccess)
+        return cuda_fail(cudaErrorUnknown);
+    for (int k = 0; k < ns; k++) {
+        if (cudaMemcpyAsync(p->hd_comp + cut[k], hc + cut[k], cut[k + 1] - cut[k], cudaMemcpyHostToDevice, p->s_in) !=
+                cudaSuccess ||
+            cudaEventRecord(p->ev_in[k], p->s_in) != cudaSuccess)
+            return cuda_fail(cudaErrorUnknown);
+    }
+    LaunchCfg cfg = ctx().cfg;
+    cfg.num_sms = p->num_sms;
+    if (wave) {
+        if (cudaStreamWaitEvent(stream, p->ev_in[0], 0) != cudaSuccess) return kErrCuda;
+        rc = enqueue_one(p->hd_comp, p->hd_out, I, p->ws, L, d_status, p->num_sms, stream);
+        if (rc) return rc;
+        if (cudaEventRecord(p->ev_dec[0], stream) != cudaSuccess) return kErrCuda;
+    } else {
+        if (aceapex_host::init_state(p->hd_state, stream)) return kErrCuda;
+        for (int k = 0; k < ns; k++) {
+            if (cudaStreamWaitEvent(stream, p->ev_in[k], 0) != cudaSuccess) return kErrCuda;
+            LaunchArgs a{};
+            a.one = make_desc(p->hd_comp, p->hd_out, I, 0);
+            a.one.n_tiles = t_beg[k + 1] - t_beg[k];
+            a.one.tile_off = t_beg[k];
+            a.one.state = p->hd_state;
+            a.one.flags = k + 1 == ns ? kDescLast : 0u;
+            a.n_streams = 1;
+            a.total_tiles = a.one.n_tiles;
+            a.wait_ns = ctx().wait_ns;
+            a.withhold = ~0ull;
+            a.max_tile_log2 = I.tile_log2;
+            a.max_n = I.decoded_len;
+            WsHead *head = (WsHead *)(p->ws + L.head);
+            StreamState *sst = (StreamState *)(p->ws + L.sst);
+            cudaError_t e = launch_flat(cfg, head, sst, (uint32_t *)(p->ws + L.flags), nullptr, a,
+                                        k + 1 == ns ? d_status : nullptr, stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (cudaEventRecord(p->ev_dec[k], stream) != cudaSuccess) return kErrCuda;
+            // this slice's output is final once its launch has completed (its sources lie before it)
+            const uint64_t o0 = t_beg[k] * T, o1 = std::min<uint64_t>(t_beg[k + 1] * T, I.decoded_len);
+            if (k + 1 < ns && o1 > o0) {
+                if (cudaStreamWaitEvent(p->s_out, p->ev_dec[k], 0) != cudaSuccess ||
+                    cudaMemcpyAsync(ho + o0, p->hd_out + o0, o1 - o0, cudaMemcpyDeviceToHost, p->s_out) != cudaSuccess)
+                    return cuda_fail(cudaErrorUnknown);
+            }
+        }
+    }
+    // the last slice (or the whole stream), then the status
+    const uint64_t o0 = wave ? 0 : t_beg[ns - 1] * T;
+    if (cudaStreamWaitEvent(p->s_out, p->ev_dec[wave ? 0 : ns - 1], 0) != cudaSuccess ||
+        cudaMemcpyAsync(ho + o0, p->hd_out + o0, I.decoded_len - o0, cudaMemcpyDeviceToHost, p->s_out) != cudaSuccess ||
+        cudaMemcpyAsync(h_status, d_status, 4, cudaMemcpyDeviceToHost, p->s_out) != cudaSuccess)
+        return cuda_fail(cudaErrorUnknown);
+    cudaError_t e = cudaStreamSynchronize(p->s_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return *h_status;
 }
 
 const char *aceapex_strerror(int code) {
