@@ -258,10 +258,9 @@ __global__ void __launch_bounds__(1024) k_wave_w(WsHead *head, StreamState *sst,
 // source [s, s + min(L, d - s)) -- have smaller indices and are found through the granule index.  In rounds,
 // every lane whose writers have all finished copies its match, out[d+k] = out[s + (k mod (d-s))], and
 // publishes depth = 1 + the writers' largest depth (nonzero: "finished").  Writers in the same 32 are seen
-// through shared memory; earlier ones through their published depth (relaxed load, then an acquire fence
-// before the source bytes are read; a writer fences its bytes before its depth).  The lowest unfinished
+// through shared memory (the warp barrier orders their bytes); earlier ones through their published depth,
+// read with an acquire load that a writer's release store of the depth, after its bytes, pairs with.  The lowest unfinished
 // match only waits on finished ones, so the persistent grid always progresses; waits are bounded.
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 constexpr int kFlowWarps = 8;
 constexpr int kFlowWidth = 32;  // lanes of one worker: a worker takes kFlowWidth consecutive matches
@@ -306,7 +305,8 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
             if (!done) {
                 // advance over finished writers; stop at the first unfinished one
                 while (w < m && __ldg(&wb.mdst[w]) < send) {
-                    const uint32_t dw = w >= m0 ? mydep[w - m0] : ld_relaxed_u32(&wb.depth[w]);
+                    // acquire: a finished writer's bytes are visible to this thread's loads below
+                    const uint32_t dw = w >= m0 ? mydep[w - m0] : ld_acquire_u32(&wb.depth[w]);
                     if (dw == 0) break;
                     mx = dw > mx ? dw : mx;
                     w++;
@@ -315,7 +315,6 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
             }
             if (__any_sync(mask, ready)) {
                 if (ready) {
-                    fence_acq_rel_gpu();
                     const uint64_t p = d - s;
                     if (p >= L) {
                         for (uint64_t o = 0; o < L; o += 16)
@@ -327,10 +326,9 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
                             if (++km == (uint32_t)p) km = 0;
                         }
                     }
-                    __threadfence();
                     uint32_t dep = mx + 1;
                     if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
-                    st_relaxed_u32(&wb.depth[m], dep);
+                    st_release_u32(&wb.depth[m], dep);  // the bytes above are visible before the depth
                     mydep[sub] = dep;
                     dmax = dep > dmax ? dep : dmax;
                     done = true;
