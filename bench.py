@@ -70,6 +70,7 @@ def stream_stats(comp: np.ndarray):
 # of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / 268435456), scaled
 # to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
 MEASURED_TRAFFIC_PER_BYTE = {
+    ("text", "k_flow"): 6.644,       # 1,427,045,632 + 356,493,312 bytes, 256 MiB deep text, one k_flow launch
     ("fastq-flat", "k_flat"): 1.856,  # 272,413,184 + 225,708,288 bytes, 256 MiB flattened FASTQ, one k_flat4 launch
 }
 
