@@ -238,8 +238,8 @@ static int ml_push(mlist *ml, uint64_t d, uint64_t s, uint32_t L) {
 static void ml_free(mlist *ml) { free(ml->d); free(ml->s); free(ml->L); memset(ml, 0, sizeof(*ml)); }
 
 /*
- * Greedy parse (§3.4 "global view").  Positions are hashed over the whole input (absolute positions, no
- * window).  The candidates for position p are the chain_limit most recent earlier positions with the same
+ * Greedy parse with a view of the whole input (§3.4): positions are hashed over all of it (absolute
+ * positions, no window).  The candidates for position p are the chain_limit most recent earlier positions with the same
  * 4-byte hash, then (if use_first) the first position ever seen with that hash.  A match never leaves its
  * destination block.  The longest candidate wins; equal lengths go to the smaller depth, then to the
  * candidate found first.

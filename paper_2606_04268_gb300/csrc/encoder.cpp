@@ -1,5 +1,5 @@
 // ACEAPEX encoder (host CPU): greedy hash-chain parse with absolute offsets over the whole input (§3.1,
-// "global view" of §3.4), self-contained blocks, chain flattening applied while parsing (§3.3) and an
+// §3.4), self-contained blocks, chain flattening applied while parsing (§3.3) and an
 // optional depth cap (§7.4); output in the ACEAPEX stream format.
 //
 // Parse rules (deterministic, so that a stream is a pure function of input and parameters):
