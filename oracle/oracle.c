@@ -239,8 +239,8 @@ static void ml_free(mlist *ml) { free(ml->d); free(ml->s); free(ml->L); memset(m
 
 /*
  * Greedy parse with a view of the whole input (§3.4): positions are hashed over all of it (absolute
- * positions, no window).  The candidates for position p are the chain_limit most recent earlier positions with the same
- * 4-byte hash, then (if use_first) the first position ever seen with that hash.  A match never leaves its
+ * positions, no window).  The candidates for position p are the chain_limit most recent earlier
+ * positions with the same 4-byte hash, then (if use_first) the first position ever seen with that hash.  A match never leaves its
  * destination block.  The longest candidate wins; equal lengths go to the smaller depth, then to the
  * candidate found first.
  *
