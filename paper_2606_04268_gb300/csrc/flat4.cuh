@@ -30,7 +30,7 @@
 namespace aceapex {
 
 constexpr uint32_t kF4Warps = 4;                              // warps per CTA
-constexpr uint32_t kF4Stage = 6144;                           // staged section bytes per warp
+constexpr uint32_t kF4Stage = 5120;                           // staged section bytes per warp
 constexpr uint32_t kF4Slack = 48;                             // readable bytes after the staged data
 constexpr uint32_t kF4LitCap = (1u << kWarpImgLog2) + 512;    // literal window staged per tile
 constexpr uint32_t kFull = 0xffffffffu;
