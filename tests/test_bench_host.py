@@ -1,0 +1,57 @@
+"""Host-side helpers of the benchmark, on CPU: stream statistics read from the block headers agree with
+the oracle's parse, the workload generators honour their stated distributions, and the serving arrival
+schedule is seeded and Poisson-shaped."""
+import numpy as np
+
+import bench
+import oracle
+import synth
+
+
+def test_stream_stats_agree_with_the_oracle_parse():
+    x = synth.make("text", 2_500_000, 7)
+    comp = oracle.encode(x, block_log2=18, min_emit=6)
+    st = bench.stream_stats(comp)
+    r, L, s, _ = oracle.parse(comp)[:4]
+    assert st["N"] == x.size and st["C"] == comp.size
+    assert st["lit_bytes"] == int(r.sum()) and st["match_bytes"] == int(L.sum())
+    assert st["n_match"] == int((L > 0).sum())
+    assert st["max_depth"] == int(oracle.depths(comp).max())
+    assert st["n_blocks"] == (x.size + (1 << 18) - 1) >> 18
+
+
+def test_kernel_bytes_are_the_stated_formulas():
+    st = dict(C=100, N=1000, match_bytes=600, lit_bytes=400, n_match=50)
+    assert bench.kernel_bytes("k_flat", st) == 100 + 1000 + 600
+    assert bench.kernel_bytes("k_flow", st) == 2 * 600 + 28 * 50
+    assert bench.kernel_bytes("k_wave", st) == 2 * 600 + 24 * 50
+    assert bench.kernel_bytes("unknown", st) == 0.0
+
+
+def test_batch_mix_follows_its_distribution():
+    mix = synth.batch_mix(4096, seed=4000)
+    sizes = np.array([n for _, n, _ in mix])
+    kinds = [k for k, _, _ in mix]
+    assert sizes.min() >= 4096 and sizes.max() <= 64 << 20
+    assert abs(np.median(sizes) / (1 << 20) - 1.0) < 0.1          # median 1 MiB
+    assert 6.5 < sizes.sum() / 2**30 < 9.5                          # ~8 GiB over 4096 streams
+    share = {k: kinds.count(k) / len(kinds) for k in ("text", "fastq", "random")}
+    assert abs(share["random"] - 0.08) < 0.02 and abs(share["text"] - 0.46) < 0.04
+    assert len({sd for _, _, sd in mix}) == len(mix)                # every stream its own seed
+
+
+def test_serve_mix_and_schedule():
+    mix = synth.serve_mix(2000, seed=5000)
+    sizes = np.array([n for _, n, _ in mix])
+    assert sizes.min() >= 64 * 1024 and sizes.max() <= 256 << 20
+    lg = np.log(sizes)
+    assert abs(np.median(lg) - (np.log(64 * 1024) + np.log(256 << 20)) / 2) < 0.3   # log-uniform
+    assert {k for k, _, _ in mix} == {"text", "fastq", "rle7"}
+    a1, w1 = bench._serve_schedule(5000, 32, 1000.0, 9)
+    a2, w2 = bench._serve_schedule(5000, 32, 1000.0, 9)
+    assert np.array_equal(a1, a2) and np.array_equal(w1, w2)        # seeded
+    gaps = np.diff(a1)
+    assert a1[0] == 0 and (gaps >= 0).all()
+    assert abs(gaps.mean() - 1e-3) < 1e-4                            # rate 1000 per second
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1                 # exponential gaps
+    assert w1.min() >= 0 and w1.max() < 32
