@@ -71,7 +71,6 @@ def stream_stats(comp: np.ndarray):
 # to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
 MEASURED_TRAFFIC_PER_BYTE = {
     ("text", "k_flow"): 6.644,       # 1,427,045,632 + 356,493,312 bytes, 256 MiB deep text, one k_flow launch
-    ("fastq-flat", "k_flat"): 1.856,  # 272,413,184 + 225,708,288 bytes, 256 MiB flattened FASTQ, one k_flat4 launch
 }
 
 
