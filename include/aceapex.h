@@ -4,13 +4,13 @@
  * ACEAPEX is an LZ77 format whose back-references are absolute positions in the decoded output and whose
  * output is cut into self-contained blocks of B bytes (paper §3.1); each block carries four arrays:
  * literal bytes, match lengths, absolute offsets and the command sequence of literal-run lengths (§3.2).
- * The byte layout is the ACEAPEX stream format, fixed once for this library.  Decoding places every sequence with a prefix sum, scatters the
- * literals and runs the match copies in dependency-depth waves (§7.1); a stream whose matches all read
- * literal bytes (chain flattening, §3.3) decodes in one pass.
+ * The byte layout is the ACEAPEX stream format, fixed once for this library.  Decoding places every
+ * sequence with a prefix sum, scatters the literals and runs the match copies in dependency order (§7.1);
+ * a stream whose matches all read literal bytes (chain flattening, §3.3) decodes in one pass.
  *
  * Conventions for every call:
  *   - pointers named d_* and the comp/out arguments of the decode calls are DEVICE pointers owned by the
- *     caller; the library never frees them;
+ *     caller; pointers named h_* are HOST pointers owned by the caller; the library never frees them;
  *   - `stream` is a cudaStream_t (passed as void*); work is enqueued on it in order;
  *   - return values are aceapex_status codes (0 = OK, negative = error); no C++ exception crosses the ABI;
  *   - malformed input never faults the GPU: every device load and store is bounds-checked and a violation
