@@ -10,12 +10,14 @@
  *                     optional chain flattening (§3.3, global or within-block) and depth cap (§7.4)
  *   oracle_serialize  writes a parse (match list) in the ACEAPEX stream format
  *   oracle_decode     the definition of the decoded bytes: blocks in order, sequences in order,
- *                     literal run then byte-by-byte match copy from the absolute source (§3.2)
+ *                     literal run then byte-by-byte match copy from the absolute source (§3.2); a
+ *                     stream whose block max_depth understates a match's depth (§7.1) is rejected
+ *                     with ERR_DEPTH after every other check
  *   oracle_parse      lists every sequence (literal-run length, match length, absolute source)
  *   oracle_lz77_rel_decode  textbook LZ77 with backward distances (§2) on the same parse
  *   oracle_depths     per-match dependency depth by byte-level simulation (§7.1)
- *   oracle_check      invariants: sources precede destinations (§3.1), flattened sources are literal
- *                     (§3.3), depth cap honoured (§7.4), header depth fields equal the recomputed ones
+ *   oracle_check      invariants: flattened sources are literal (§3.3), depth cap honoured (§7.4),
+ *                     block depth fields equal the recomputed ones (§7.1)
  *
  * Pins (tests/test_oracle_*.py): encode->decode round trip on every generator, agreement with the
  * textbook relative decoder, brute force over every legal parse of tiny strings, hand-assembled golden
@@ -419,12 +421,10 @@ static int read_block(const uint8_t *c, const or_info *I, uint64_t b, blk_t *k) 
  * `seq_r/seq_L/seq_s/lits` are given, lists the sequences instead (seq_L = 0 when the sequence has no
  * match).  Validates every rule of the stream format, sync table included.
  */
-static int walk(const uint8_t *c, uint64_t comp_len, uint8_t *out, uint64_t out_len, uint64_t *seq_r, uint64_t *seq_L,
-                uint64_t *seq_s, uint8_t *lits, uint64_t cap_seq, uint64_t *n_seq_out) {
-    or_info I;
-    int rc = oracle_peek(c, comp_len, &I);
-    if (rc) return rc;
-    if (out && I.N != out_len) return OR_ERR_SIZE;
+static int walk_(const uint8_t *c, const or_info *Ip, uint8_t *out, uint32_t *wd, uint64_t *seq_r, uint64_t *seq_L,
+                 uint64_t *seq_s, uint8_t *lits, uint64_t cap_seq, uint64_t *n_seq_out) {
+    const or_info I = *Ip;
+    int rc, depth_lie = 0;
     const uint64_t B = 1ull << I.block_log2, T = 1ull << I.tile_log2;
     uint64_t si = 0, li = 0, tot_match = 0, tot_seq = 0;
     uint32_t max_depth = 0;
@@ -466,6 +466,15 @@ static int walk(const uint8_t *c, uint64_t comp_len, uint8_t *out, uint64_t out_
             if (has_match) {
                 if (s >= pos) return OR_ERR_OFFSET;
                 if (out) for (uint64_t j = 0; j < L; j++) out[pos + j] = out[s + j];
+                if (wd) {
+                    /* depth (format §4, paper §7.1): 1 + the deepest byte of the effective source; literal
+                       bytes are 0 (wd is zero-filled and literal bytes are never rewritten) */
+                    uint64_t eff = L < pos - s ? L : pos - s;
+                    uint32_t mx = 0;
+                    for (uint64_t x = s; x < s + eff; x++) if (wd[x] > mx) mx = wd[x];
+                    for (uint64_t j = 0; j < L; j++) wd[pos + j] = mx + 1;
+                    if (mx + 1 > k.max_depth) depth_lie = 1;
+                }
                 pos += L;
             }
             if (seq_r) {
@@ -478,8 +487,28 @@ static int walk(const uint8_t *c, uint64_t comp_len, uint8_t *out, uint64_t out_
             return OR_ERR_FORMAT;
     }
     if (tot_match != I.n_match || tot_seq != I.n_seq || max_depth != I.max_depth) return OR_ERR_FORMAT;
+    /* a block whose max_depth is below the depth of one of its matches: the stream is malformed (format §4),
+       reported after every other error, as the last check of the stream */
+    if (depth_lie) return OR_ERR_DEPTH;
     if (n_seq_out) *n_seq_out = si;
     return OR_OK;
+}
+
+/* `out` given: decode, and track every byte's depth to validate the blocks' max_depth fields. */
+static int walk(const uint8_t *c, uint64_t comp_len, uint8_t *out, uint64_t out_len, uint64_t *seq_r, uint64_t *seq_L,
+                uint64_t *seq_s, uint8_t *lits, uint64_t cap_seq, uint64_t *n_seq_out) {
+    or_info I;
+    int rc = oracle_peek(c, comp_len, &I);
+    if (rc) return rc;
+    if (out && I.N != out_len) return OR_ERR_SIZE;
+    uint32_t *wd = NULL;
+    if (out) {
+        wd = (uint32_t *)calloc(I.N ? I.N : 1, sizeof(uint32_t));
+        if (!wd) return OR_ERR_NOMEM;
+    }
+    rc = walk_(c, &I, out, wd, seq_r, seq_L, seq_s, lits, cap_seq, n_seq_out);
+    free(wd);
+    return rc;
 }
 
 int oracle_decode(const uint8_t *comp, uint64_t comp_len, uint8_t *out, uint64_t out_len) {
@@ -549,13 +578,14 @@ done:
 
 /*
  * Invariants of a stream: 0 when all hold, else the first failing one:
- *   1  a source does not precede its destination (§3.1)
- *   2  a block's max_depth differs from the recomputed one
- *   3  the stream's max_depth differs from the recomputed one
+ *   2  a block's max_depth differs from the recomputed one (§7.1)
  *   4  global flattening: a match reads a non-literal byte (§3.3)
  *   5  block flattening: a match reads a non-literal byte of its own block (§3.3)
  *   6  a match deeper than the depth cap (§7.4)
- * negative: the stream does not parse.
+ * negative: the stream does not parse.  Two further invariants need no code of their own: a source that
+ * does not precede its destination (§3.1) fails the parse (ERR_OFFSET), and a stream whose max_depth is
+ * not the largest block max_depth fails it too (ERR_FORMAT), so once every block passes 2 the stream's
+ * max_depth equals the recomputed one.
  */
 int oracle_check(const uint8_t *comp, uint64_t comp_len) {
     or_info I;
@@ -574,14 +604,12 @@ int oracle_check(const uint8_t *comp, uint64_t comp_len) {
         const uint64_t B = 1ull << I.block_log2;
         uint64_t pos = 0, nb = I.n_blocks;
         uint32_t *bdepth = (uint32_t *)calloc(nb ? nb : 1, 4);
-        uint32_t smax = 0;
         res = 0;
         for (uint64_t i = 0; i < (uint64_t)n && !res; i++) {
             for (uint64_t j = 0; j < r[i]; j++) { islit[pos + j] = 1; wd[pos + j] = 0; }
             pos += r[i];
             if (!L[i]) continue;
             uint64_t d = pos;
-            if (s[i] >= d) { res = 1; break; }
             uint64_t eff = L[i] < d - s[i] ? L[i] : d - s[i];
             uint32_t mx = 0;
             for (uint64_t x = s[i]; x < s[i] + eff; x++) {
@@ -592,7 +620,6 @@ int oracle_check(const uint8_t *comp, uint64_t comp_len) {
             if (res) break;
             for (uint64_t k = 0; k < L[i]; k++) { wd[d + k] = mx + 1; islit[d + k] = 0; }
             if (mx + 1 > bdepth[d / B]) bdepth[d / B] = mx + 1;
-            if (mx + 1 > smax) smax = mx + 1;
             if (I.depth_cap && mx + 1 > I.depth_cap) res = 6;
             pos += L[i];
         }
@@ -601,7 +628,6 @@ int oracle_check(const uint8_t *comp, uint64_t comp_len) {
             if (read_block(comp, &I, b, &k)) { res = OR_ERR_FORMAT; break; }
             if (k.max_depth != bdepth[b]) res = 2;
         }
-        if (!res && smax != I.max_depth) res = 3;
         free(bdepth);
     }
 done:

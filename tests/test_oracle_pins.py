@@ -4,7 +4,9 @@
 * agreement with the textbook relative-distance LZ77 decoder (§2) on the same parse (§3.1 equivalence);
 * brute force: every legal parse of every tiny string decodes to that string (separate file);
 * invariants the paper fixes: sources precede destinations (§3.1), flattened sources are literal bytes
-  (§3.3), depth cap honoured (§7.4), header depths equal an independent depth computation (§7.1);
+  (§3.3, global and within-block), depth cap honoured (§7.4), header depths equal an independent depth
+  computation (§7.1); every return code of oracle_check is made to fire by a planted violation;
+* a stream whose depth fields understate its matches' depths is rejected by the decoder (ERR_DEPTH);
 * malformed streams are rejected with the error code the stream format assigns (format §5).
 """
 import numpy as np
@@ -140,3 +142,84 @@ def test_malformed_streams_rejected():
     d0 = int(r[0])
     bad = _mut(comp, o_off, int(w), min(d0 + 1, (1 << (8 * int(w))) - 1))
     assert oracle.decode_rc(bad)[0] == -4
+
+
+# ---------------------------------------------------------------------------------------------- depth fields
+def _block_offsets(comp):
+    nb = int.from_bytes(bytes(comp[24:32]), "little")
+    return [int.from_bytes(bytes(comp[64 + 8 * b:72 + 8 * b]), "little") for b in range(nb)]
+
+
+def _set_depths(comp, block_depths, stream_depth):
+    """Overwrite the blocks' and the stream's max_depth fields (format §1.1, §2.1)."""
+    c = comp.copy()
+    for off, dep in zip(_block_offsets(c), block_depths):
+        c[off + 24:off + 28] = np.frombuffer(int(dep).to_bytes(4, "little"), np.uint8)
+    c[48:52] = np.frombuffer(int(stream_depth).to_bytes(4, "little"), np.uint8)
+    return c
+
+
+def lower_depths(comp, to=1):
+    """Every depth field clipped to `to`: a stream whose headers understate its matches' depths."""
+    offs = _block_offsets(comp)
+    deps = [min(int.from_bytes(bytes(comp[o + 24:o + 28]), "little"), to) for o in offs]
+    return _set_depths(comp, deps, max(deps, default=0))
+
+
+# two blocks of 16 bytes; block 0: (d 4, s 0, L 4) depth 1 and (d 9, s 0, L 4) depth 1; block 1: (d 20, s 4,
+# L 4) reads match bytes of block 0, depth 2
+_X2 = np.frombuffer(b"abcdabcdXabcdYYYZZZZabcdQQQQQQQQ", dtype=np.uint8)
+
+
+def test_block_flatten_invariant_detects_violation():
+    """Within-block flattening (§3.3): a match may read match bytes of an earlier block, never of its own."""
+    ok = oracle.serialize(_X2, [4, 9, 20], [0, 0, 4], [4, 4, 4], flatten=1, block_log2=4, tile_log2=2)
+    assert oracle.check(ok) == 0 and np.array_equal(oracle.decode(ok), _X2)
+    assert list(oracle.depths(ok)) == [1, 1, 2]
+    bad = oracle.serialize(_X2, [4, 9, 20], [0, 4, 4], [4, 4, 4], flatten=1, block_log2=4, tile_log2=2)
+    assert oracle.check(bad) == 5
+    assert np.array_equal(oracle.decode(bad), _X2)            # a valid stream, only the flag is wrong
+    # the same parse under the global flag breaks invariant 4 first (the read from block 0's match)
+    glob = oracle.serialize(_X2, [4, 9, 20], [0, 0, 4], [4, 4, 4], flatten=2, block_log2=4, tile_log2=2)
+    assert oracle.check(glob) == 4
+
+
+def test_header_depth_fields_checked():
+    """Block max_depth fields must equal the recomputed depths (§7.1): over- and understatement."""
+    comp = oracle.serialize(_X2, [4, 9, 20], [0, 0, 4], [4, 4, 4], block_log2=4, tile_log2=2)
+    assert oracle.peek(comp).max_depth == 2 and oracle.check(comp) == 0
+    over = _set_depths(comp, [1, 3], 3)
+    assert oracle.check(over) == 2
+    assert oracle.decode_rc(over)[0] == 0                      # overstating is harmless to a decoder
+    over0 = _set_depths(comp, [2, 2], 2)
+    assert oracle.check(over0) == 2
+    under = _set_depths(comp, [1, 1], 1)
+    assert oracle.check(under) == 2
+    assert oracle.decode_rc(under)[0] == -8                    # ERR_DEPTH
+    zero = _set_depths(comp, [0, 2], 2)                        # block 0 has matches, field says none
+    assert oracle.decode_rc(zero)[0] == -8
+    # the stream field must still be the largest block field, else the stream is malformed
+    assert oracle.decode_rc(_set_depths(comp, [1, 2], 1))[0] == -2
+
+
+def test_depth_lie_reported_after_other_errors():
+    """ERR_DEPTH is the last check of a stream: a format error anywhere else wins."""
+    x = synth.make("text", 40_000, 4)
+    comp = oracle.encode(x, block_log2=12, tile_log2=8)
+    assert oracle.peek(comp).max_depth >= 2
+    lie = lower_depths(comp, 1)
+    assert oracle.decode_rc(lie)[0] == -8
+    offs = _block_offsets(lie)
+    bad = _mut(lie, offs[-1] + 32 + 20 + 16, 4, 1)             # last block, sync entry 1 out_pos
+    assert oracle.decode_rc(bad)[0] == -2
+
+
+@pytest.mark.parametrize("kind", ["text", "markov", "rle7"])
+def test_depth_lie_on_generated_streams(kind):
+    """Depth-2 streams (cap 2) whose fields are lowered to 1 are rejected; cap-1 streams are not."""
+    x = synth.make(kind, 200_000, 6)
+    comp = oracle.encode(x, block_log2=14, tile_log2=10, depth_cap=2)
+    assert oracle.peek(comp).max_depth == 2
+    assert oracle.decode_rc(lower_depths(comp, 1))[0] == -8
+    flat = oracle.encode(x, block_log2=14, tile_log2=10, flatten=2)
+    assert oracle.decode_rc(lower_depths(flat, 1))[0] == 0
