@@ -31,26 +31,37 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 MiB, GiB = 1 << 20, 1 << 30
+
+# Encoder parameters of each content kind.  FASTQ uses a 12-byte key chain (on a 4-letter alphabet 4-byte
+# keys take few values) and a longer shortest match (a DNA match shorter than 12 bytes hardly saves space).
+FLAT = {"text": dict(flatten=2, min_emit=6), "markov": dict(flatten=2, min_emit=6), "rle7": dict(flatten=2, min_emit=6),
+        "random": dict(flatten=2), "fastq": dict(flatten=2, min_emit=12, long_bits=26, chain_limit=4)}
+CAP4 = {"text": dict(depth_cap=4, min_emit=6), "fastq": dict(depth_cap=4, min_emit=12, long_bits=26, chain_limit=4)}
+
 WORKLOADS = {
     # name: (generator kind, size, encoder params, description)
     "text": ("text", GiB, dict(min_emit=6),
              "1 GiB synthetic English-like text (Zipf s=1.0, 200k words), full-depth unflattened chains"),
-    "fastq-flat": ("fastq", GiB, dict(flatten=2, min_emit=6),
+    "fastq-flat": ("fastq", GiB, FLAT["fastq"],
                    "1 GiB synthetic FASTQ (150-base reads, 64 x 1 Mb references, Q30 Gaussian qualities), "
                    "chain-flattened (global)"),
-    "fastq-cap4": ("fastq", GiB, dict(depth_cap=4, min_emit=6), "1 GiB synthetic FASTQ, depth cap 4"),
-    "text-flat": ("text", GiB, dict(flatten=2, min_emit=6),
+    "fastq-cap4": ("fastq", GiB, CAP4["fastq"], "1 GiB synthetic FASTQ, depth cap 4"),
+    "text-flat": ("text", GiB, FLAT["text"],
                   "1 GiB synthetic English-like text (Zipf s=1.0, 200k words), chain-flattened (global)"),
     "small": ("markov", 4 * MiB, dict(min_match=4), "4 MiB Markov text, 4 blocks, min match 4, unflattened"),
-    # multi-stream workloads (run_batch / run_serve)
-    "batch": (None, 0, dict(flatten=2, min_emit=6),
+    # multi-stream workloads (run_batch / run_serve): payloads encoded with FLAT of their kind
+    "batch": (None, 0, None,
               "batched decode: 4096 streams, lognormal sizes (median 1 MiB, clipped 4 KiB-64 MiB, ~8 GiB), "
               "46% text / 46% FASTQ / 8% uniform random, chain-flattened, one persistent launch replayed as a "
               "CUDA graph with an autotuned launch shape"),
-    "serve": (None, 0, dict(flatten=2, min_emit=6),
+    "serve": (None, 0, None,
               "serving loop: Poisson arrivals, log-uniform sizes 64 KiB-256 MiB, text / FASTQ / period-7 RLE "
               "(self-overlapping matches), chain-flattened, HBM admission budget 64 GiB, continuous batching"),
 }
+# measured beside the batch in the default run: the single-stream configurations, each at its full size
+EXTRAS = ("fastq-flat", "fastq-cap4", "text")
+BATCH_STREAMS, BATCH_UNIQUE = 4096, 256
+SERVE_POOL = 32
 
 
 def stream_stats(comp: np.ndarray):
@@ -69,23 +80,30 @@ def stream_stats(comp: np.ndarray):
 # DRAM bytes (read + write) per decoded byte of the dominant kernel, from one ncu capture of a 256 MiB case
 # of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / 268435456), scaled
 # to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
-MEASURED_TRAFFIC_PER_BYTE = {
-    ("text", "k_flow"): 6.644,       # 1,427,045,632 + 356,493,312 bytes, 256 MiB deep text, one k_flow launch
-}
+# DRAM bytes (read + write) per decoded byte of the dominant kernel, from one ncu capture of a 256 MiB case
+# of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / decoded bytes),
+# scaled to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
+MEASURED_TRAFFIC_PER_BYTE = {}
 
 
 def kernel_bytes(name: str, st: dict) -> float:
-    """Algorithmic HBM bytes of one launch of each kernel (stream read once, output written once, each
-    match-source byte read once, per-match metadata of the wavefront path at its stored width)."""
-    C, N, M, L, nm = st["C"], st["N"], st["match_bytes"], st["lit_bytes"], st["n_match"]
+    """The method's HBM bytes of one launch of each kernel: the stream read once, each output byte written
+    once, each match-source byte read once (the wavefront's parse writes the whole output, its match copies
+    read and write the match bytes).  Per-match metadata is not the method's and is in metadata_bytes."""
+    C, N, M, L = st["C"], st["N"], st["match_bytes"], st["lit_bytes"]
     return {
-        "k_flat": C + N + M,                          # stream, output, match sources
-        "k_parse": C + L + 24 * nm + N / 16,          # stream, literals, 24 B records, granule index
-        "k_depth": 40 * nm,                           # records + writer lookups + depth
-        "k_wave": 2 * M + 24 * nm,                    # sources, destinations, queue + records
-        "k_flow": 2 * M + 28 * nm,                    # sources, destinations, records + granule index, depth
-        "k_scatter": 8 * nm, "k_hist": 4 * nm,
+        "k_flat": C + N + M,        # stream, output, match sources
+        "k_parse": C + N,           # stream, output (literals and the match bytes' placeholders)
+        "k_wave": 2 * M,            # match sources, match bytes
+        "k_flow": 2 * M,
     }.get(name, 0.0)
+
+
+def metadata_bytes(name: str, st: dict) -> float:
+    """Bytes of the wavefront path's own per-match metadata a kernel moves (not counted as the method's)."""
+    nm, N = st["n_match"], st["N"]
+    return {"k_parse": 24 * nm + N / 16, "k_flow": 28 * nm, "k_wave": 24 * nm, "k_depth": 40 * nm,
+            "k_scatter": 44 * nm, "k_hist": 4 * nm}.get(name, 0.0)
 
 
 class ClockSampler:
@@ -295,73 +313,171 @@ def dist_setup():
     return world, rank, local
 
 
-def run_reference_multi(args):
-    """Reference arm of the multi-stream workloads: the oracle decoder on the host cores, each step a
-    bounded sample (whole streams of the workload's payload pool, in order, about 2 s of CPU work)."""
-    if args.workload == "batch":
-        mix = synth.batch_mix(256, seed=4000)
-        specs = [(k, n, sd, dict(flatten=2, min_emit=6) if k != "random" else dict(flatten=2)) for k, n, sd in mix]
-    else:
-        specs = [(k, n, sd, dict(flatten=2, min_emit=6)) for k, n, sd in synth.serve_mix(32, seed=5000)]
-    import paper_2606_04268_gb300 as ax
-    ax.build()
-    pool = encode_pool(specs)
+REF_SAMPLE_BYTES = 12 * MiB  # decoded bytes the reference arm's oracle encodes and decodes per step
+
+
+def _reference_sample(args):
+    """Input bytes and oracle-encoded streams of a bounded sample of the workload, plus the workload's config
+    (the same dict as the GPU arm's).  Only the oracle and the seeded generators are used: a block-aligned
+    prefix of a single-stream workload, or the first payloads of a multi-stream workload's pool."""
     import oracle
     oracle.build()
-    i, times, nbytes = 0, [], []
-    for step in range(args.warmup + args.steps):
-        t, b = 0.0, 0
-        while t < 2.0:
-            x, comp = pool[i % len(pool)]
-            i += 1
-            t0 = time.perf_counter()
-            rc, _ = oracle.decode_rc(comp, x.size)
-            t += time.perf_counter() - t0
-            b += x.size
-            assert rc == 0
-        if step >= args.warmup:
-            times.append(t); nbytes.append(b)
-    v = sum(nbytes) / sum(times) / 1e9
-    line = {"impl": "reference", "metric": "decoded GB/s", "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload][3]},
-            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "whole streams of the workload's payload pool, ~2 s of CPU work per step"},
-            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    world = args.gpus
+    if args.workload == "batch":
+        specs, which, N = batch_plan_specs(0)
+        cfg = batch_config(world, N)
+    elif args.workload == "serve":
+        specs = [(k, n, sd, FLAT[k]) for k, n, sd in synth.serve_mix(SERVE_POOL, seed=5000)]
+        cfg = serve_config(world)
+    else:
+        kind, n, enc, _ = WORKLOADS[args.workload]
+        n = args.size or n
+        block = 1 << enc.get("block_log2", 20)
+        cut = min(n, max(block, REF_SAMPLE_BYTES // block * block))
+        x = synth.make(kind, n, stream_seed(kind, 0))[:cut].copy()
+        return [(x, oracle.encode(x, **enc))], single_config(args, world), \
+            f"the first {cut} bytes of the workload's input (whole 1 MiB blocks), oracle-encoded"
+    pool, total = [], 0
+    for k, n, sd, enc in specs:
+        if total >= REF_SAMPLE_BYTES:
+            break
+        x = synth.make(k, n, sd)
+        pool.append((x, oracle.encode(x, **enc)))
+        total += n
+    return pool, cfg, f"the first {len(pool)} payloads of the workload's pool ({total} bytes), oracle-encoded"
 
 
 def run_reference(args):
+    """The reference arm: the oracle decoder as it stands, on the host cores, each step one decode of a
+    bounded sample of the workload.  Under torchrun only rank 0 runs."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    if args.workload in ("batch", "serve"):
-        run_reference_multi(args)
-        return
-    x, comp, desc, _ = make_stream(args, 0)
     import oracle
-    oracle.build()
+    pool, cfg, sample = _reference_sample(args)
     for _ in range(args.warmup):
-        rc, _ = oracle.decode_rc(comp, x.size)
-        assert rc == 0
-    times = []
+        for x, comp in pool:
+            assert oracle.decode_rc(comp, x.size)[0] == 0
+    times, nb = [], sum(x.size for x, _ in pool)
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        rc, out = oracle.decode_rc(comp, x.size)
+        for x, comp in pool:
+            rc, out = oracle.decode_rc(comp, x.size)
+            assert rc == 0
         times.append(time.perf_counter() - t0)
-        assert rc == 0
-    assert np.array_equal(out, x)
+    assert np.array_equal(out, pool[-1][0])
     t = sum(times) / len(times)
-    v = x.size / t / 1e9
+    v = nb / t / 1e9
     line = {"impl": "reference", "metric": "decoded GB/s", "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": desc, "decoded_bytes": int(x.size), "comp_bytes": int(comp.size)},
-            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"the whole workload stream ({x.size} decoded bytes) per step"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _levels(ax, d_comp, out, stream, st):
+    """Per-level depth histogram summary (§7.1 levels; the blocking call reads the statistics back)."""
+    if st["max_depth"] <= 1:
+        return None
+    ax.decode(d_comp, out, stream)
+    hs = ax.get_stats()
+    h = np.asarray(hs["level_hist"], dtype=np.int64)
+    if h.size <= 1 or h[1:].sum() == 0:
+        return None
+    lv = np.arange(h.size)
+    cum = np.cumsum(h[1:]) / h[1:].sum()
+    return {"max_depth": int(hs["n_levels"]), "mean_depth": round(float((lv[1:] * h[1:]).sum() / h[1:].sum()), 2),
+            "p50": int(np.searchsorted(cum, 0.5)) + 1, "p90": int(np.searchsorted(cum, 0.9)) + 1,
+            "p99": int(np.searchsorted(cum, 0.99)) + 1, "matches_at_depth_1_to_10": h[1:11].tolist()}
+
+
+def _roofline(prof, st, steps, hbm_peak, peak_kind, workload):
+    """Dominant kernel of a step and its achieved bandwidth (the method's bytes / its CUDA-event time)."""
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms = kern[dom][0] / kern[dom][1]
+    ach = kernel_bytes(dom, st) / (dom_ms * 1e-3) / 1e9
+    key = (workload, dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(ach / hbm_peak, 4), "peak_kind": peak_kind,
+            "algorithmic_bytes": round(kernel_bytes(dom, st)), "metadata_bytes": round(metadata_bytes(dom, st)),
+            "traffic": round(MEASURED_TRAFFIC_PER_BYTE[key] * st["N"]) if key in MEASURED_TRAFFIC_PER_BYTE else None}
+    match_ms = sum(kern[k][0] / kern[k][1] for k in ("k_flow", "k_depth", "k_hist", "k_levels", "k_scatter", "k_wave")
+                   if k in kern)
+    return roof, {k: round(v[0] / v[1], 4) for k, v in kern.items()}, match_ms, \
+        int(sum(v[1] for v in kern.values()) // steps * steps)
+
+
+def measure_stream(ax, torch, x, comp, steps, warmup, hbm_peak, peak_kind, workload, barrier, e2e=True):
+    """K back-to-back decodes of one device-resident stream (aceapex_decode_async, one workspace), the same K
+    with per-kernel CUDA events, the level histogram and, with e2e, the host-buffer call."""
+    st = stream_stats(comp)
+    info = ax.peek_header(comp[:64])
+    d_comp = torch.from_numpy(comp).cuda()
+    out = torch.empty(x.size, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(ax.workspace_size(info), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ax.decode_async(d_comp, out, info, ws, status, stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0, ax.STATUS_NAMES.get(int(status.item()))
+    assert torch.equal(out, torch.from_numpy(x).cuda()), "decoded bytes differ from the input"
+    # timed region: K decodes back to back (inputs and outputs exceed L2 several times)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / steps
+    assert int(status.item()) == 0
+    ax.profile(True)
+    for _ in range(steps):
+        step()
+    prof = ax.profile_read()
+    ax.profile(False)
+    roof, kms, match_ms, launches = _roofline(prof, st, steps, hbm_peak, peak_kind, workload)
+    r = {"ms": round(ms, 4), "gbs": round(st["N"] / (ms * 1e-3) / 1e9, 3),
+         "decode_roofline_frac": round((st["C"] + 2 * st["N"]) / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+         "decoded_bytes": st["N"], "comp_bytes": st["C"], "ratio": round(st["C"] / st["N"], 4),
+         "max_depth": st["max_depth"], "n_match": st["n_match"],
+         "mean_match": round(st["match_bytes"] / max(st["n_match"], 1), 2),
+         "path": "one-pass" if st["max_depth"] <= 1 else "wavefront", "roofline": roof, "kernels_ms": kms,
+         "gpu_launches": launches, "levels": _levels(ax, d_comp, out, stream, st),
+         "match_phase": ({"ms": round(match_ms, 4), "gbs": round(st["N"] / (match_ms * 1e-3) / 1e9, 3),
+                          "kernels": "depth and match copies after the parse, literal scatter excluded"}
+                         if match_ms > 0 else None)}
+    if e2e:
+        # end to end through the public host-buffer call (aceapex_decode_host): every step copies the stream
+        # from pinned host memory to the device and the decoded bytes back, overlapped with the decode
+        h_comp = torch.from_numpy(comp).pin_memory()
+        h_out = torch.empty(x.size, dtype=torch.uint8).pin_memory()
+        e2e_steps = max(1, min(steps, 10))
+        ax.decode_host(h_comp, h_out, stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ax.decode_host(h_comp, h_out, stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        assert torch.equal(h_out, torch.from_numpy(x))
+        r["e2e"] = {"value": round(st["N"] / e2e_s / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": st["C"],
+                    "d2h_bytes_per_step": st["N"]}
+    del d_comp, out, ws
+    return r
+
+
+def single_config(args, world):
+    kind, n, enc, desc = WORKLOADS[args.workload]
+    return {"workload": desc, "decoded_bytes": args.size or n, "parallelism": f"replicas x{world}",
+            "l2": "inputs and outputs larger than L2 (no flush needed)"}
 
 
 def run_ours(args):
@@ -376,16 +492,6 @@ def run_ours(args):
     if args.wave_scheduler is not None:
         ax.set_wave_scheduler(args.wave_scheduler)
     x, comp, desc, enc_s = make_stream(args, rank)
-    st = stream_stats(comp)
-    info = ax.peek_header(comp[:64])
-    d_comp = torch.from_numpy(comp).cuda()
-    out = torch.empty(x.size, dtype=torch.uint8, device="cuda")
-    ws = torch.zeros(ax.workspace_size(info), dtype=torch.uint8, device="cuda")
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step():
-        ax.decode_async(d_comp, out, info, ws, status, stream)
 
     def barrier():
         if world > 1:
@@ -394,101 +500,29 @@ def run_ours(args):
 
     hbm_peak, peak_kind = peaks()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        assert int(status.item()) == 0, ax.STATUS_NAMES.get(int(status.item()))
-        assert torch.equal(out, torch.from_numpy(x).cuda()), "decoded bytes differ from the input"
-        # timed region: K decodes back to back (inputs and outputs exceed L2 several times)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        assert int(status.item()) == 0
-        # the same K decodes with CUDA events around every library kernel: per-kernel launch durations
-        ax.profile(True)
-        for _ in range(args.steps):
-            step()
-        prof = ax.profile_read()
-        ax.profile(False)
-        # per-level depth histogram (§7.1 levels; the blocking call reads the statistics back)
-        levels = None
-        if st["max_depth"] > 1:
-            ax.decode(d_comp, out, stream)
-            hs = ax.get_stats()
-            h = np.asarray(hs["level_hist"], dtype=np.int64)
-            if h.size > 1 and h[1:].sum() > 0:
-                lv = np.arange(h.size)
-                cum = np.cumsum(h[1:]) / h[1:].sum()
-                levels = {"max_depth": int(hs["n_levels"]), "mean_depth": round(float((lv[1:] * h[1:]).sum() / h[1:].sum()), 2),
-                          "p50": int(np.searchsorted(cum, 0.5)) + 1, "p90": int(np.searchsorted(cum, 0.9)) + 1,
-                          "p99": int(np.searchsorted(cum, 0.99)) + 1, "matches_at_depth_1_to_10": h[1:11].tolist()}
-        # end to end through the public host-buffer call (aceapex_decode_host): every step copies the stream
-        # from pinned host memory to the device and the decoded bytes back, overlapped with the decode
-        h_comp = torch.from_numpy(comp).pin_memory()
-        h_out = torch.empty(x.size, dtype=torch.uint8).pin_memory()
-        e2e_steps = max(1, min(args.steps, 10))
-        ax.decode_host(h_comp, h_out, stream)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            ax.decode_host(h_comp, h_out, stream)
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        assert torch.equal(h_out, torch.from_numpy(x))
-    ms = max_over_ranks(ms, world, "cuda")
+        r = measure_stream(ax, torch, x, comp, args.steps, args.warmup, hbm_peak, peak_kind, args.workload, barrier)
+    ms = max_over_ranks(r["ms"], world, "cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
-    total_bytes = st["N"] * world
-    value = total_bytes / (ms * 1e-3) / 1e9
-    # dominant kernel of a step
-    kern = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(kern, key=lambda k: kern[k][0])
-    dom_ms = kern[dom][0] / kern[dom][1]
-    ach = kernel_bytes(dom, st) / (dom_ms * 1e-3) / 1e9
-    decode_frac = (st["C"] + 2 * st["N"]) / (ms * 1e-3) / 1e9 / hbm_peak
-    # the paper's GPU figures time the match phase only (literals preloaded): the same cut of ours
-    match_ms = sum(kern[k][0] / kern[k][1] for k in ("k_flow", "k_depth", "k_hist", "k_levels", "k_scatter", "k_wave")
-                   if k in kern)
-    line = {
-        "metric": "decoded GB/s", "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": desc, "decoded_bytes": st["N"], "comp_bytes": st["C"], "ratio": round(st["C"] / st["N"], 4),
-                   "max_depth": st["max_depth"], "n_match": st["n_match"], "path": "one-pass" if st["max_depth"] <= 1 else "wavefront",
-                   "wave_scheduler": args.wave_scheduler,
-                   "parallelism": f"replicas x{world}", "l2": "inputs and outputs larger than L2 (no flush needed)",
-                   "encode_s": round(enc_s, 1)},
-        "decode_roofline_frac": round(decode_frac, 4),
-        "match_phase": ({"ms": round(match_ms, 4), "gbs": round(st["N"] / (match_ms * 1e-3) / 1e9, 3),
-                         "kernels": "depth and match copies after the parse, literal scatter excluded"}
-                        if match_ms > 0 else None),
-        "levels": levels,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(ach / hbm_peak, 4), "peak_kind": peak_kind,
-                     "traffic": (round(MEASURED_TRAFFIC_PER_BYTE[(args.workload, dom)] * st["N"])
-                                 if (args.workload, dom) in MEASURED_TRAFFIC_PER_BYTE else None)},
-        "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in kern.items()},
-        "gpu_launches": int(sum(v[1] for v in kern.values()) // args.steps * args.steps),
-        "e2e": {"value": round(st["N"] / e2e_s / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": st["C"],
-                "d2h_bytes_per_step": st["N"]},
-        "clocks": clk.summary(),
-    }
+    value = r["decoded_bytes"] * world / (ms * 1e-3) / 1e9
+    line = _base_line(args, value, ms, desc, {k: v for k, v in single_config(args, world).items() if k != "workload"})
+    line["details"] = {k: r[k] for k in ("decoded_bytes", "comp_bytes", "ratio", "max_depth", "n_match", "mean_match",
+                                         "path")}
+    line["details"].update(wave_scheduler=args.wave_scheduler, encode_s=round(enc_s, 1))
+    for k in ("decode_roofline_frac", "match_phase", "levels", "roofline", "kernels_ms", "gpu_launches", "e2e"):
+        line[k] = r[k]
+    line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu:
-        v, reps, secs = cpu_oracle_baseline(comp, st["N"], args.cpu_seconds)
+        v, reps, secs = cpu_oracle_baseline(comp, r["decoded_bytes"], args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"the workload's stream decoded {reps} times ({secs:.1f} s)"}
         if args.cpu_all_cores:
-            r = cpu_oracle_all_cores(comp, st["N"])
-            if r:
+            rr = cpu_oracle_all_cores(comp, r["decoded_bytes"])
+            if rr:
                 line["cpu_baseline_all_cores"] = {
-                    "value": round(r[0], 4), "unit": "GB/s", "cores": r[1], "kind": "oracle",
-                    "sample": f"one decode of the workload's stream per core, all at once ({r[2]:.1f} s wall)"}
+                    "value": round(rr[0], 4), "unit": "GB/s", "cores": rr[1], "kind": "oracle",
+                    "sample": f"one decode of the workload's stream per core, all at once ({rr[2]:.1f} s wall)"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -518,6 +552,29 @@ def _cpu_sample(comps, xs, seconds):
     return done / t_total / 1e9, n_streams, done, t_total
 
 
+def batch_plan_specs(rank: int):
+    """The batch workload: payload specs (kind, size, seed, encoder params), which payload each of the 4096
+    streams carries, and the decoded bytes of all streams."""
+    mix = synth.batch_mix(BATCH_UNIQUE, seed=4000 + rank)
+    specs = [(k, n, sd, FLAT[k]) for k, n, sd in mix]
+    which = [i % BATCH_UNIQUE for i in range(BATCH_STREAMS)]  # stream i carries payload i mod 256
+    return specs, which, int(sum(specs[u][1] for u in which))
+
+
+def batch_config(world: int, N: int):
+    return {"workload": WORKLOADS["batch"][3], "streams": BATCH_STREAMS, "distinct_payloads": BATCH_UNIQUE,
+            "decoded_bytes": N, "parallelism": f"replicas x{world}",
+            "l2": "inputs and outputs larger than L2 (no flush needed)"}
+
+
+def _start_extras():
+    """Encode the extra single-stream workloads into the file cache in the background (spawned workers)."""
+    import multiprocessing as mp
+    specs = [(WORKLOADS[w][0], WORKLOADS[w][1], stream_seed(WORKLOADS[w][0], 0), WORKLOADS[w][2]) for w in EXTRAS]
+    pool = mp.get_context("spawn").Pool(len(specs))
+    return pool, pool.map_async(_warm_cache, specs, chunksize=1)
+
+
 def run_batch(args):
     """4096 streams decoded by one persistent launch per step (CUDA-graph replay of a batch plan)."""
     import torch
@@ -527,23 +584,24 @@ def run_batch(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
+    extras = args.extras and world == 1 and rank == 0
+    ext_pool, ext_job = _start_extras() if extras else (None, None)
     torch.cuda.set_device(local)
     ax.build()
-    n_streams, n_unique = 4096, 256
-    enc = WORKLOADS["batch"][2]
-    mix = synth.batch_mix(n_unique, seed=4000 + rank)
+    specs, which, N = batch_plan_specs(rank)
     t0 = time.time()
-    pool = encode_pool([(k, n, sd, enc if k != "random" else dict(flatten=2)) for k, n, sd in mix])
+    pool = encode_pool(specs)
     enc_s = time.time() - t0
     xs = [p[0] for p in pool]
     cs = [p[1] for p in pool]
-    which = [i % n_unique for i in range(n_streams)]          # stream i carries payload i mod 256
+    n_streams = len(which)
     c_off = np.zeros(n_streams + 1, np.int64)
     o_off = np.zeros(n_streams + 1, np.int64)
     for i, u in enumerate(which):
         c_off[i + 1] = c_off[i] + cs[u].size                   # stream sizes are multiples of 16
         o_off[i + 1] = o_off[i] + xs[u].size
-    C, N = int(c_off[-1]), int(o_off[-1])
+    C = int(c_off[-1])
+    assert int(o_off[-1]) == N
     d_unique = [torch.from_numpy(c).cuda() for c in cs]
     d_comp = torch.empty(C, dtype=torch.uint8, device="cuda")
     for i, u in enumerate(which):
@@ -615,35 +673,54 @@ def run_batch(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t1
         assert (plan.statuses(stream) == 0).all()
+    plan.close()
     ms = max_over_ranks(ms, world, "cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
     value = N * world / (ms * 1e-3) / 1e9
-    kern = {k: v for k, v in prof.items() if v[1] > 0}
     n_lit = sum(stream_stats(cs[u])["lit_bytes"] for u in which)
-    st = {"C": C, "N": N, "match_bytes": N - n_lit, "lit_bytes": n_lit, "n_match": 0}
-    dom = max(kern, key=lambda k: kern[k][0])
-    dom_ms = kern[dom][0] / kern[dom][1]
-    ach = kernel_bytes(dom, st) / (dom_ms * 1e-3) / 1e9
-    line = _base_line(args, value, ms, WORKLOADS["batch"][3], {
-        "streams": n_streams, "distinct_payloads": n_unique, "decoded_bytes": N, "comp_bytes": C,
-        "ratio": round(C / N, 4), "parallelism": f"replicas x{world}",
-        "l2": "inputs and outputs larger than L2 (no flush needed)",
-        "autotuned": {"kernel": cfg[0], "threads": cfg[1], "ctas_per_sm": cfg[2], "seqs_per_thread": cfg[3]},
-        "plain_one_at_a_time_gbs": round(N / (plain_ms * 1e-3) / 1e9, 3),
-        "batched_vs_plain": round(plain_ms / ms, 3), "encode_s": round(enc_s, 1)})
+    n_match = sum(stream_stats(cs[u])["n_match"] for u in which)
+    st = {"C": C, "N": N, "match_bytes": N - n_lit, "lit_bytes": n_lit, "n_match": n_match}
+    roof, kms, _, launches = _roofline(prof, st, args.steps, hbm_peak, peak_kind, "batch")
+    line = _base_line(args, value, ms, WORKLOADS["batch"][3],
+                      {k: v for k, v in batch_config(world, N).items() if k != "workload"})
+    line["details"] = {"comp_bytes": C, "ratio": round(C / N, 4), "n_match": n_match,
+                       "mean_match": round((N - n_lit) / max(n_match, 1), 2),
+                       "autotuned": {"warps_per_cta": cfg[0], "ctas_per_sm": cfg[1]},
+                       "plain_one_at_a_time_gbs": round(N / (plain_ms * 1e-3) / 1e9, 3),
+                       "batched_vs_plain": round(plain_ms / ms, 3), "encode_s": round(enc_s, 1)}
     line["decode_roofline_frac"] = round((C + 2 * N) / (ms * 1e-3) / 1e9 / hbm_peak, 4)
-    line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                        "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind}
-    line["kernels_ms"] = {k: round(v[0] / v[1], 4) for k, v in kern.items()}
-    line["gpu_launches"] = int(sum(v[1] for v in kern.values()) // args.steps * args.steps)
+    line["roofline"] = roof
+    line["kernels_ms"] = kms
+    line["gpu_launches"] = launches
     line["e2e"] = {"value": round(N / e2e_s / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": C, "d2h_bytes_per_step": N}
     line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu:
         v, ns, nb, secs = _cpu_sample(cs, xs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"the first {ns} distinct streams of the batch ({nb} bytes, {secs:.1f} s)"}
+    del d_comp, d_out, comps, outs, h_comp, h_out
+    torch.cuda.empty_cache()
+    if extras:
+        # the single-stream configurations at their full size, each with its own dominant-kernel roofline
+        t0 = time.time()
+        ext_job.get()
+        ext_pool.close()
+        ext_pool.join()
+        wait_s = time.time() - t0
+        res = {}
+        with ClockSampler(torch.cuda.current_device()) as clk2:
+            for w in EXTRAS:
+                kind, n, enc, desc = WORKLOADS[w]
+                x, comp, _ = cached_stream(kind, n, stream_seed(kind, 0), enc)
+                r = measure_stream(ax, torch, x, comp, args.steps, args.warmup, hbm_peak, peak_kind, w, barrier,
+                                   e2e=False)
+                r["workload"] = desc
+                res[w] = r
+        res["clocks"] = clk2.summary()
+        res["encode_wait_s"] = round(wait_s, 1)
+        line["workloads"] = res
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -720,6 +797,11 @@ def _serve_plain(ax, torch, pool_dev, sizes, arrivals, which, verify=None):
 LOADS = (0.3, 0.5, 0.7, 0.9, 1.1, 1.5)  # offered load, as a fraction of one-at-a-time plain capacity
 
 
+def serve_config(world: int):
+    return {"workload": WORKLOADS["serve"][3], "pool_payloads": SERVE_POOL, "offered_loads": list(LOADS),
+            "parallelism": f"replicas x{world}"}
+
+
 def run_serve(args):
     """Poisson arrivals into the continuous-batching server vs one-request-at-a-time plain decode."""
     import torch
@@ -730,11 +812,10 @@ def run_serve(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     ax.build()
-    n_pool, n_req = 32, max(200, 50 * args.steps)
-    enc = WORKLOADS["serve"][2]
+    n_pool, n_req = SERVE_POOL, max(200, 50 * args.steps)
     mix = synth.serve_mix(n_pool, seed=5000 + rank)
     t0 = time.time()
-    pool = encode_pool([(k, n, sd, enc) for k, n, sd in mix])
+    pool = encode_pool([(k, n, sd, FLAT[k]) for k, n, sd in mix])
     enc_s = time.time() - t0
     xs = [p[0] for p in pool]
     cs = [p[1] for p in pool]
@@ -784,12 +865,13 @@ def run_serve(args):
     best = max(tps_list, key=lambda k: sat[f"served_tps{k}"]["gbs"])
     served = sat[f"served_tps{best}"]
     ms = served["span_ms"] / n_req  # per request
-    line = _base_line(args, served["gbs"] * world, ms, WORKLOADS["serve"][3], {
-        "pool_payloads": n_pool, "requests_per_run": n_req, "mean_service_ms_alone": round(1e3 * mean_svc, 3),
+    line = _base_line(args, served["gbs"] * world, ms, WORKLOADS["serve"][3],
+                      {k: v for k, v in serve_config(world).items() if k != "workload"})
+    line["details"] = {
+        "requests_per_run": n_req, "mean_service_ms_alone": round(1e3 * mean_svc, 3),
         "by_offered_load": {str(k): v for k, v in results.items()}, "tiles_per_step": best,
         "value_is": "aggregate GB/s of the served run at offered load 1.5 (of one-at-a-time capacity), "
-                    "best tiles_per_step",
-        "parallelism": f"replicas x{world}", "encode_s": round(enc_s, 1)})
+                    "best tiles_per_step", "encode_s": round(enc_s, 1)}
     line["e2e"] = {"value": served["gbs"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                    "note": "requests arrive device-resident (serving keeps inputs and outputs in HBM)"}
     line["gpu_launches"] = None
@@ -809,7 +891,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="text", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="batch", choices=list(WORKLOADS))
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="batch workload: skip the single-stream configurations measured beside it")
     ap.add_argument("--size", type=int, default=0, help="override the workload size (bytes)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")

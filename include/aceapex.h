@@ -69,15 +69,21 @@ typedef struct {
     uint64_t phase_cycles[8];
 } aceapex_stats;
 
-/* Host-side header parse.  host_prefix holds at least the first 64 bytes of the stream.
- * Checks magic, version, flags and field ranges (stream format §1.1). */
+/* Host-side header parse (paper §3.1: the stream is a sequence of self-contained blocks; the header gives
+ * their size and count, and the depth information of §7.1 that picks the decode schedule).  host_prefix
+ * holds at least the first 64 bytes of the stream.  Checks magic, version, flags and field ranges (stream
+ * format §1.1); returns ACEAPEX_ERR_FORMAT / ACEAPEX_ERR_SIZE on a bad header, ACEAPEX_ERR_ARG on null. */
 int aceapex_peek_header(const void *host_prefix, size_t len, aceapex_info *info);
 
 /* Device workspace bytes needed by aceapex_decode_async for this stream. */
 size_t aceapex_workspace_size(const aceapex_info *info);
 
 /*
- * Decode one stream (blocking).  comp: device bytes of the stream, 16-byte aligned, comp_len bytes.
+ * Decode one stream (blocking) -- the operation of paper §3.1-§3.2: every sequence of every block is placed
+ * by a prefix sum of its literal-run and match lengths, its literal run is copied from lit[], and each
+ * match copies bytes from an absolute position of the output ("copy N bytes from position P"), matches of
+ * increasing dependency depth after the ones they read (§7.1).  comp: device bytes of the stream, 16-byte
+ * aligned, comp_len bytes.
  * out: device buffer of out_len bytes, which must equal the header's decoded length.  Reads the 64-byte
  * header back to the host, takes workspace from a cached pool, enqueues the decode on `stream`,
  * synchronises `stream` and returns the device status.
@@ -85,7 +91,9 @@ size_t aceapex_workspace_size(const aceapex_info *info);
 int aceapex_decode(const void *comp, size_t comp_len, void *out, size_t out_len, void *stream);
 
 /*
- * Decode one stream without any host synchronisation.  info: from aceapex_peek_header on a host copy of
+ * Decode one stream without any host synchronisation (the same operation as aceapex_decode, paper §3.1-§3.2,
+ * §7.1; the caller supplies the workspace and receives the status on the device).  info: from
+ * aceapex_peek_header on a host copy of
  * the header.  d_ws: caller-owned device workspace of at least aceapex_workspace_size(info) bytes,
  * zero-filled before its first use (it may then be reused without clearing by calls that do not
  * overlap in time).  d_status: device int32 that receives the status.  Returns an argument error at
@@ -98,10 +106,11 @@ int aceapex_decode_async(const void *comp, size_t comp_len, void *out, size_t ou
  * Decode one stream without allocating anything (the paper has no counterpart: this serves callers that
  * cannot allocate device memory while decoding -- a process whose memory was budgeted up front, real-time
  * code, or a library that must not use the application's allocator).  Same arguments as
- * aceapex_decode_async minus the workspace: the scratch is a 1 MiB array in the library's static device
- * memory, which every GPU that loads the library holds until the process exits.  Only streams whose
- * matches all have depth <= 1 (chain-flattened), with tiles of at most 4 KiB and at most 261,888 tiles
- * (about 1 GiB of output at 4 KiB tiles), fit: anything else returns ACEAPEX_ERR_NOMEM at once.  The
+ * aceapex_decode_async minus the workspace: the scratch is a 16 MiB array in the library's static device
+ * memory, which every GPU that loads the library holds until the process exits.  It holds a flag per tile
+ * and the literal bitmap (one bit per output byte), so only streams whose matches all have depth <= 1
+ * (chain-flattened), with tiles of at most 4 KiB and flags plus bitmap within 16 MiB (about 127 MiB of
+ * output at 4 KiB tiles), fit: anything else returns ACEAPEX_ERR_NOMEM at once.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  Every call on a device shares the one array: calls that overlap on the
  * GPU race and must not be issued (serialise them on one stream).  Enqueued on `stream`, no host
@@ -115,7 +124,7 @@ int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *out, size_t 
  * h_comp: comp_len bytes of an ACEAPEX stream in host memory; h_out: out_len = decoded length bytes of host
  * memory; both are the caller's and are only read / written during the call.  The library copies the
  * stream to device memory it owns (kept for later calls, grown on demand), decodes, and copies the output
- * back.  One-pass streams (depth <= 1) are cut into up to 16 slices of whole blocks: a slice's stream
+ * back.  Streams the one-pass kernel takes are cut into up to 16 slices of whole blocks: a slice's stream
  * bytes are copied in, its tiles decoded and its output copied out on three CUDA streams, so transfers in
  * both directions overlap the decode.  Deeper streams are copied, decoded whole, and copied back.  With
  * pinned (page-locked) buffers the copies are asynchronous; pageable buffers work but serialise.  Work
@@ -126,10 +135,12 @@ int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *out, size_t 
 int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t out_len, void *stream);
 
 /*
- * Decode n independent streams (blocking).  comps/outs: host arrays of n device pointers; comp_lens and
- * out_lens: host arrays; statuses: host array of n int32 that receives each stream's status.  Streams
- * whose matches all have depth <= 1 are decoded together by one persistent launch over a global tile
- * queue; the others are decoded one after another.  Returns 0 when every stream decoded, else the first
+ * Decode n independent streams (blocking) -- paper §7.5: streams have no dependency on each other, so they
+ * decode together without any exchange; each stream is decoded as in aceapex_decode (§3.1-§3.2, §7.1).
+ * comps/outs: host arrays of n device pointers; comp_lens and
+ * out_lens: host arrays; statuses: host array of n int32 that receives each stream's status.  The streams
+ * the one-pass kernel takes (see aceapex_set_force_wavefront) are decoded together by one persistent launch
+ * over a global tile queue; the others are decoded one after another.  Returns 0 when every stream decoded, else the first
  * failing status.
  */
 int aceapex_decode_batch(int n, const void *const *comps, const size_t *comp_lens, void *const *outs,
@@ -148,18 +159,10 @@ int aceapex_batch_plan_launch(aceapex_batch_plan *plan, int graph, void *stream)
 int aceapex_batch_plan_statuses(aceapex_batch_plan *plan, int32_t *statuses, void *stream);
 int aceapex_batch_plan_destroy(aceapex_batch_plan *plan);
 
-/* Launch shape of the one-pass kernel: threads per CTA (128, 256 or 512), CTAs per SM (0 = as many as
- * fit), sequences per thread per parse chunk (2, 4 or 8).  Applies to later launches on this context. */
-int aceapex_set_launch_config(int threads, int ctas_per_sm, int seqs_per_thread);
-int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *seqs_per_thread);
-
-/* One-pass kernel variant: 0 one warp per tile, used when every tile is at most 4 KiB, else
- * variant 1; 1 one CTA per tile with a 16 KiB shared-memory image (tiles up to 16 KiB, else variant 2);
- * 2 one CTA per tile storing bytes straight to HBM (any tile size); 3 one warp per tile with the tile's
- * sections staged in shared memory by bulk copies and word-merged copies, 32 sequences per warp step
- * (tiles up to 4 KiB and streams up to ~4 GiB, else variant 0); 4 the same with 128 sequences per warp
- * step, four per lane.  The default is 3.  Returns ACEAPEX_ERR_ARG for another value. */
-int aceapex_set_one_pass_kernel(int kind);
+/* Launch shape of the one-pass kernel: warps per CTA (2, 4 or 8; default 4) and CTAs per SM (0 = as many as
+ * fit, the default).  Applies to later launches on this context.  Returns ACEAPEX_ERR_ARG for another value. */
+int aceapex_set_launch_config(int warps_per_cta, int ctas_per_sm);
+int aceapex_get_launch_config(int *warps_per_cta, int *ctas_per_sm);
 
 /* Scheduler of streams whose matches are deeper than 1: 1 per-level work queues drained level by level
  * by one persistent cooperative kernel with a bounded grid barrier between levels; 0 dataflow: each
@@ -169,8 +172,11 @@ int aceapex_set_one_pass_kernel(int kind);
  * bytes.  Returns ACEAPEX_ERR_ARG for another value. */
 int aceapex_set_wave_scheduler(int kind);
 
-/* Decode every stream with the wavefront path, even streams whose max_depth <= 1 would take the one-pass
- * kernel (for testing and comparison).  Applies to later calls on this context. */
+/* Decode every stream with the wavefront path, even streams the one-pass kernel would take (for testing
+ * and comparison).  Applies to later calls on this context.  The one-pass kernel takes the streams whose
+ * max_depth is at most 1, with tiles of at most 4 KiB and at most 0xFFF00000 bytes of output; it checks
+ * every source byte against the literal bitmap it builds, so a stream whose depth fields understate its
+ * matches' depths ends in ACEAPEX_ERR_DEPTH on either path. */
 int aceapex_set_force_wavefront(int on);
 
 /* Limit of every bounded device wait in nanoseconds (0 restores the default of 4 s).  withhold_tile is a
@@ -200,10 +206,14 @@ const char *aceapex_strerror(int code);
  * hbm_budget and one of max_slots slots is free (the server allocates each output with the stream-ordered
  * allocator), then enqueues ONE one-pass launch that advances every admitted request by a slice of its tiles
  * (each request gets an equal share of tiles_per_step); requests admitted while others are running join the
- * next launch.  A stream deeper than 1 is decoded whole in the step that admits it.  poll returns 1 once a
+ * next launch.  A stream the one-pass kernel does not take (deeper than 1, tiles over 4 KiB) is decoded
+ * whole in the step that admits it.  poll returns 1 once a
  * request's last launch has completed (with its status and output pointer), 0 while pending; release frees
  * its output and budget (stream-ordered on `stream`).  step returns the number of queued + running
- * requests.  One host thread drives a server; the budget counts stream + output bytes.
+ * requests.  One host thread drives a server; the budget counts stream + output bytes (plus, for a request
+ * the one-pass kernel takes, its literal bitmap: one bit per output byte).  A request is admitted only once
+ * its first work is enqueued: if that fails, step returns the error and the request stays queued, holding
+ * nothing.
  */
 typedef struct aceapex_server aceapex_server;
 int aceapex_server_create(size_t hbm_budget, int max_slots, uint64_t tiles_per_step, aceapex_server **server);
@@ -215,16 +225,20 @@ int aceapex_server_destroy(aceapex_server *server);
 
 /* ------------------------------------------------------------------------------------------- encoder */
 /* Encoder parameters (host side, CPU).  Defaults: block_log2 20, tile_log2 12, min_match 4,
- * hash_bits 20, chain_limit 16, flatten 0, depth_cap 0, use_first 1, min_emit 0. */
+ * hash_bits 20, chain_limit 16, flatten 0, depth_cap 0, use_first 1, min_emit 0, long_bits 0 (off),
+ * long_chain 4.  long_bits > 0 adds a second candidate chain keyed by the 12 bytes at each position
+ * (2^long_bits hash values, long_chain most recent positions each, tried first), which finds long repeats
+ * on small alphabets (DNA bases) where 4-byte keys take few values. */
 typedef struct {
     uint32_t block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit;
+    uint32_t long_bits, long_chain;
 } aceapex_enc_params;
 
 /*
  * Encode n host bytes into a newly allocated host buffer (*out, release with aceapex_free).  Greedy
  * hash-chain parse with absolute offsets (§3.1, §3.4), optional chain flattening (§3.3) and depth cap
  * (§7.4).  Returns the stream length or a negative status.  Inputs must be shorter than 4 GiB;
- * chain_limit <= 16, 8 <= hash_bits <= 24.
+ * chain_limit <= 16, 8 <= hash_bits <= 24; long_bits 0 or 8..28 with 1 <= long_chain <= 16.
  */
 int64_t aceapex_encode(const void *in, size_t n, const aceapex_enc_params *params, void **out);
 void aceapex_free(void *p);

@@ -33,7 +33,8 @@ class OracleError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("block_log2", "tile_log2", "min_match", "hash_bits", "chain_limit", "flatten", "depth_cap", "use_first", "min_emit")]
+                ("block_log2", "tile_log2", "min_match", "hash_bits", "chain_limit", "flatten", "depth_cap", "use_first", "min_emit",
+                 "long_bits", "long_chain")]
 
 
 class Info(ctypes.Structure):
@@ -80,8 +81,9 @@ def _load():
 
 
 def params(block_log2=20, tile_log2=12, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
-           depth_cap=0, use_first=1, min_emit=0) -> Params:
-    return Params(block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit)
+           depth_cap=0, use_first=1, min_emit=0, long_bits=0, long_chain=4) -> Params:
+    return Params(block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit,
+                  long_bits, long_chain)
 
 
 def _u8(a) -> np.ndarray:

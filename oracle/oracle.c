@@ -38,11 +38,14 @@
 #define MAGIC 0x58454341u
 #define NONE UINT64_MAX
 #define CHAIN_MAX 256
+#define LONG_CHAIN_MAX 16
+#define LONG_KEY 12
 #define PERIOD_MAX 16
 #define PERIOD_RESTART 32
 
 typedef struct {
     uint32_t block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit;
+    uint32_t long_bits, long_chain;
 } or_params;
 
 typedef struct {
@@ -222,6 +225,13 @@ static uint32_t hash4(const uint8_t *p, uint32_t bits) {
     return (uint32_t)(v * 2654435761u) >> (32 - bits);
 }
 
+/* Hash of the 12 bytes at p (little-endian 8-byte and 4-byte words, multiplied and added mod 2^64). */
+static uint32_t hash12(const uint8_t *p, uint32_t bits) {
+    uint64_t lo = rd(p, 8), hi = rd(p + 8, 4);
+    uint64_t v = lo * 0x9E3779B97F4A7C15ull + hi * 0xC2B2AE3D27D4EB4Full;
+    return (uint32_t)(v >> (64 - bits));
+}
+
 typedef struct { uint64_t *d, *s; uint32_t *L; uint64_t n, cap; } mlist;
 static int ml_push(mlist *ml, uint64_t d, uint64_t s, uint32_t L) {
     if (ml->n == ml->cap) {
@@ -241,9 +251,13 @@ static void ml_free(mlist *ml) { free(ml->d); free(ml->s); free(ml->L); memset(m
 
 /*
  * Greedy parse with a view of the whole input (§3.4): positions are hashed over all of it (absolute
- * positions, no window).  The candidates for position p are the chain_limit most recent earlier
- * positions with the same 4-byte hash, then (if use_first) the first position ever seen with that hash.  A match never leaves its
- * destination block.  The longest candidate wins; equal lengths go to the smaller depth, then to the
+ * positions, no window).  The candidates for position p are, when long_bits is set, the long_chain most
+ * recent earlier positions with the same hash of the 12 bytes at p (a key that stays selective on small
+ * alphabets such as DNA, where 4-byte keys take few values), then the chain_limit most recent earlier
+ * positions with the same 4-byte hash, then (if use_first) the first position ever seen with that hash.
+ * Every position is entered in the 4-byte chain; in flatten modes only literal positions (their own root)
+ * enter the 12-byte chain, so that its candidates start on bytes a flattened match may point at.  A match
+ * never leaves its destination block.  The longest candidate wins; equal lengths go to the smaller depth, then to the
  * candidate found first.
  *
  * Chain flattening (§3.3) is applied while parsing: every byte x carries root[x], the literal position
@@ -261,15 +275,20 @@ static int greedy_parse(const uint8_t *in, uint64_t N, const or_params *prm, mli
     const uint32_t bits = prm->hash_bits ? prm->hash_bits : 20;
     const uint64_t HS = 1ull << bits;
     const int flat = (int)prm->flatten, bl = (int)prm->block_log2;
+    const uint32_t lbits = prm->long_bits;
+    const uint64_t LS = lbits ? 1ull << lbits : 1;
     uint64_t *head = (uint64_t *)malloc(HS * 8), *first = (uint64_t *)malloc(HS * 8);
     uint64_t *prev = (uint64_t *)malloc((N ? N : 1) * 8);
+    uint64_t *head2 = (uint64_t *)malloc(LS * 8), *prev2 = lbits ? (uint64_t *)malloc((N ? N : 1) * 8) : NULL;
     uint64_t *root = flat ? (uint64_t *)malloc((N ? N : 1) * 8) : NULL;
     uint32_t *wdepth = (uint32_t *)calloc(N ? N : 1, 4);
-    if (!head || !first || !prev || !wdepth || (flat && !root)) {
-        free(head); free(first); free(prev); free(root); free(wdepth);
+#define FREE_ALL() do { free(head); free(first); free(prev); free(head2); free(prev2); free(root); free(wdepth); } while (0)
+    if (!head || !first || !prev || !head2 || (lbits && !prev2) || !wdepth || (flat && !root)) {
+        FREE_ALL();
         return OR_ERR_NOMEM;
     }
     for (uint64_t i = 0; i < HS; i++) { head[i] = NONE; first[i] = NONE; }
+    for (uint64_t i = 0; i < LS; i++) head2[i] = NONE;
     const uint64_t mm = prm->min_match > prm->min_emit ? prm->min_match : prm->min_emit, cap = prm->depth_cap;
     uint64_t p = 0;
 #define R(x) ((flat == 2 || ((x) >> bl) == (p >> bl)) ? root[x] : (x))
@@ -280,10 +299,16 @@ static int greedy_parse(const uint8_t *in, uint64_t N, const or_params *prm, mli
         uint32_t best_dep = 0;
         if (maxL >= mm && p + 4 <= N) {
             uint32_t h = hash4(in + p, bits);
-            /* candidate list: the chain's most recent positions, then the first position of this hash */
-            uint64_t cand[CHAIN_MAX + 1];
+            /* candidate list: the long-key chain's most recent positions, the 4-byte chain's most recent
+               positions, then the first position of the 4-byte hash */
+            uint64_t cand[LONG_CHAIN_MAX + CHAIN_MAX + 1];
             uint32_t nc = 0;
-            for (uint64_t c = head[h]; c != NONE && nc < prm->chain_limit; c = prev[c]) cand[nc++] = c;
+            if (lbits && p + LONG_KEY <= N) {
+                uint32_t nl = 0;
+                for (uint64_t c = head2[hash12(in + p, lbits)]; c != NONE && nl < prm->long_chain; c = prev2[c])
+                    cand[nc++] = c, nl++;
+            }
+            for (uint64_t c = head[h], k = 0; c != NONE && k < prm->chain_limit; c = prev[c], k++) cand[nc++] = c;
             if (prm->use_first && first[h] != NONE) cand[nc++] = first[h];
             for (uint32_t j = 0; j < nc; j++) {
                 uint64_t c = cand[j], Lc = 0, src = c;
@@ -319,7 +344,7 @@ static int greedy_parse(const uint8_t *in, uint64_t N, const or_params *prm, mli
         }
         if (best_L >= mm) {
             if (ml_push(ml, p, best_s, (uint32_t)best_L)) {
-                free(head); free(first); free(prev); free(root); free(wdepth);
+                FREE_ALL();
                 return OR_ERR_NOMEM;
             }
             uint64_t per = p - best_s;
@@ -341,18 +366,25 @@ static int greedy_parse(const uint8_t *in, uint64_t N, const or_params *prm, mli
                 prev[q] = head[h]; head[h] = q;
                 if (first[h] == NONE) first[h] = q;
             }
+            if (lbits && q + LONG_KEY <= N && (!flat || root[q] == q)) {
+                uint32_t h2 = hash12(in + q, lbits);
+                prev2[q] = head2[h2]; head2[h2] = q;
+            }
         }
         p += adv;
     }
 #undef R
-    free(head); free(first); free(prev); free(root); free(wdepth);
+    FREE_ALL();
+#undef FREE_ALL
     return OR_OK;
 }
 
 int64_t oracle_encode(const uint8_t *in, uint64_t N, const or_params *prm, uint8_t **out) {
     *out = NULL;
     if (prm->block_log2 < 2 || prm->block_log2 > 24 || prm->min_match < 1 || prm->flatten > 2 ||
-        prm->chain_limit > CHAIN_MAX || (prm->hash_bits && (prm->hash_bits < 8 || prm->hash_bits > 28)))
+        prm->chain_limit > CHAIN_MAX || (prm->hash_bits && (prm->hash_bits < 8 || prm->hash_bits > 28)) ||
+        (prm->long_bits && (prm->long_bits < 8 || prm->long_bits > 28 || prm->long_chain < 1 ||
+                            prm->long_chain > LONG_CHAIN_MAX)))
         return OR_ERR_ARG;
     mlist ml = {0};
     int rc = greedy_parse(in, N, prm, &ml);

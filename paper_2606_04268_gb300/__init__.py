@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libaceapex.so")
 _SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp"]
-_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "flat2.cuh", "flat3.cuh", "flat4.cuh", "flat5.cuh", "wave.cuh"]
+_HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "warp_tile.cuh", "onepass.cuh", "wave.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 OK, ERR_ARG, ERR_FORMAT, ERR_SIZE, ERR_OFFSET, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_DEPTH = 0, -1, -2, -3, -4, -5, -6, -7, -8
@@ -104,7 +104,7 @@ class Stats(ctypes.Structure):
 class EncParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("block_log2", "tile_log2", "min_match", "hash_bits", "chain_limit", "flatten", "depth_cap",
-                 "use_first", "min_emit")]
+                 "use_first", "min_emit", "long_bits", "long_chain")]
 
 
 # every exported symbol of include/aceapex.h
@@ -112,7 +112,7 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_decode_noalloc",
            "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
            "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
-           "aceapex_decode_host", "aceapex_get_launch_config", "aceapex_set_one_pass_kernel", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
+           "aceapex_decode_host", "aceapex_get_launch_config", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
            "aceapex_server_release", "aceapex_server_destroy",
@@ -142,10 +142,9 @@ def lib():
             L.aceapex_batch_plan_launch.argtypes = [p, i32, p]
             L.aceapex_batch_plan_statuses.argtypes = [p, p, p]
             L.aceapex_batch_plan_destroy.argtypes = [p]
-            L.aceapex_set_launch_config.argtypes = [i32, i32, i32]
-            L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
+            L.aceapex_set_launch_config.argtypes = [i32, i32]
+            L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 2
             L.aceapex_set_force_wavefront.argtypes = [i32]
-            L.aceapex_set_one_pass_kernel.argtypes = [i32]
             L.aceapex_decode_host.argtypes = [p, sz, p, sz, p]
             L.aceapex_set_wave_scheduler.argtypes = [i32]
             L.aceapex_set_wait_limit.argtypes = [u64, u64]
@@ -378,23 +377,20 @@ def _wrap_ptr(ptr: int, n: int):
     return torch.as_tensor(_Holder(), device="cuda")
 
 
-def set_launch_config(threads: int = 256, ctas_per_sm: int = 0, seqs_per_thread: int = 4) -> None:
-    _check(lib().aceapex_set_launch_config(threads, ctas_per_sm, seqs_per_thread), "aceapex_set_launch_config")
+def set_launch_config(warps_per_cta: int = 4, ctas_per_sm: int = 0) -> None:
+    """Launch shape of the one-pass kernel: warps per CTA (2, 4 or 8) and CTAs per SM (0 = as many as fit)."""
+    _check(lib().aceapex_set_launch_config(int(warps_per_cta), int(ctas_per_sm)), "aceapex_set_launch_config")
 
 
 def get_launch_config():
-    t, c, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().aceapex_get_launch_config(ctypes.byref(t), ctypes.byref(c), ctypes.byref(s)), "get_launch_config")
-    return t.value, c.value, s.value
-
-
-def set_one_pass_kernel(kind: int) -> None:
-    """0: warp per tile (default, tiles <= 4 KiB); 1: CTA per tile with a 16 KiB image; 2: CTA per tile, direct."""
-    _check(lib().aceapex_set_one_pass_kernel(int(kind)), "aceapex_set_one_pass_kernel")
+    w, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().aceapex_get_launch_config(ctypes.byref(w), ctypes.byref(c)), "get_launch_config")
+    return w.value, c.value
 
 
 def set_wave_scheduler(kind: int) -> None:
-    """1: per-level queues with a grid barrier per level (default); 0: per-match dataflow."""
+    """Scheduler of the wavefront path: 2 warp dataflow (default); 1 per-level queues with a grid barrier
+    per level; 0 per-match dataflow."""
     _check(lib().aceapex_set_wave_scheduler(int(kind)), "aceapex_set_wave_scheduler")
 
 
@@ -435,11 +431,12 @@ PHASE_NAMES = ["open", "parse", "literals", "store_publish", "wait", "matches", 
 
 
 def encode(data, block_log2=20, tile_log2=12, min_match=4, hash_bits=20, chain_limit=16, flatten=FLAT_NONE,
-           depth_cap=0, use_first=1, min_emit=0) -> np.ndarray:
+           depth_cap=0, use_first=1, min_emit=0, long_bits=0, long_chain=4) -> np.ndarray:
     """Encode host bytes with the library's CPU encoder; returns the stream as a uint8 numpy array."""
     a = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data)
     assert a.dtype == np.uint8
-    prm = EncParams(block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit)
+    prm = EncParams(block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit,
+                    long_bits, long_chain)
     ptr = ctypes.c_void_p()
     n = lib().aceapex_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(prm), ctypes.byref(ptr))
     if n < 0:

@@ -1,15 +1,12 @@
 """Launch-shape autotuner for batched decodes.
 
-The tunable knobs of the one-pass path are:
-- the kernel variant: one warp per tile reading the compressed sections from global memory, or one warp
-  per tile with the sections staged in shared memory by bulk copies, at 32 or 128 sequences per warp step;
-- the number of CTAs per SM (occupancy cap of the persistent grid);
-- for streams whose tiles exceed 4 KiB, the CTA shape of the CTA-per-tile kernel: threads per CTA and
-  sequences per thread per parse chunk.
+The tunable knobs of the one-pass path are the CTA shape of the persistent grid -- warps per CTA (2, 4 or
+8; each warp decodes one tile at a time, 32 sequences per step) -- and the number of CTAs per SM (the
+occupancy cap).  The chunk width, the tile of the stream format, is fixed by the encoder.
 
-The tuner times every candidate on the caller's plan (CUDA events, plain launches) and keeps the
-fastest. Results are cached in a JSON file keyed by the device and a signature of the batch, so a serving
-process tunes once per batch shape.
+The tuner times every candidate on the caller's plan (CUDA events, plain launches) and keeps the fastest.
+Results are cached in a JSON file keyed by the device and a signature of the batch, so a serving process
+tunes once per batch shape.  The configuration that was in force before is restored if timing fails.
 """
 from __future__ import annotations
 
@@ -18,17 +15,20 @@ import os
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
-# (one-pass kernel variant, threads, ctas per SM, sequences per thread)
-CANDIDATES = [(k, t, c, s) for k in (3, 4, 0) for c in (0, 4, 3, 2) for (t, s) in ((256, 4),)] + \
-             [(3, t, 0, s) for (t, s) in ((128, 4), (256, 2), (256, 8), (512, 2))]
+# (warps per CTA, CTAs per SM); 0 = as many CTAs as fit
+CANDIDATES = [(w, c) for w in (4, 2, 8) for c in (0, 4, 3, 2)]
 
 
 def apply(cfg) -> None:
     """Make `cfg` the launch configuration of later launches on this context."""
-    from . import set_launch_config, set_one_pass_kernel
-    kernel, threads, ctas, spt = cfg
-    set_one_pass_kernel(kernel)
-    set_launch_config(threads, ctas, spt)
+    from . import set_launch_config
+    warps, ctas = cfg
+    set_launch_config(warps, ctas)
+
+
+def current():
+    from . import get_launch_config
+    return tuple(get_launch_config())
 
 
 def _device_key() -> str:
@@ -55,10 +55,11 @@ def _event_timer(plan, reps: int):
 
 
 def tune(plan, signature: str, reps: int = 3, cache_path: str = DEFAULT_CACHE, candidates=None,
-         force: bool = False, timer=None, device_key: str | None = None, apply_fn=apply):
+         force: bool = False, timer=None, device_key: str | None = None, apply_fn=apply, current_fn=current):
     """Pick the fastest launch configuration for `plan`; applies it and returns (cfg, {cfg: ms}).
 
-    timer(cfg) -> ms and device_key replace the CUDA-event timing and the device lookup (tests)."""
+    timer(cfg) -> ms, device_key, apply_fn and current_fn replace the CUDA-event timing, the device lookup
+    and the library calls (tests)."""
     key = f"{device_key or _device_key()}|{signature}"
     cache = {}
     if os.path.exists(cache_path):
@@ -73,9 +74,15 @@ def tune(plan, signature: str, reps: int = 3, cache_path: str = DEFAULT_CACHE, c
         return cfg, {tuple(k): v for k, v in cache[key].get("ms", [])}
     timer = timer or _event_timer(plan, reps)
     times = {}
-    for cfg in candidates or CANDIDATES:
-        apply_fn(cfg)
-        times[tuple(cfg)] = float(timer(tuple(cfg)))
+    before = current_fn() if current_fn else None
+    try:
+        for cfg in candidates or CANDIDATES:
+            apply_fn(cfg)
+            times[tuple(cfg)] = float(timer(tuple(cfg)))
+    except BaseException:
+        if before is not None:
+            apply_fn(before)
+        raise
     best = min(times, key=times.get)
     apply_fn(best)
     cache[key] = {"cfg": list(best), "ms": [[list(k), v] for k, v in times.items()]}

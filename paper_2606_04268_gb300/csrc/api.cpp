@@ -58,12 +58,13 @@ constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct WsLayout {
-    size_t head, sst, flags, descs, status, block_base, mdst, msrc, mlen, depth, queue, gidx, qd, qs, ql, hist, lvl, cursor, total;
+    size_t head, sst, flags, litmap, descs, status, block_base, bdepth, mdst, msrc, mlen, depth, queue, gidx, qd, qs, ql,
+        hist, lvl, cursor, total;
 };
 
-// Regions of a workspace.  One-pass: flags per tile.  Wavefront: per-match records, granule index,
-// per-level arrays.
-WsLayout layout(int n_streams, uint64_t total_tiles, bool wave, const aceapex_info *wi) {
+// Regions of a workspace.  One-pass: flags per tile and the literal bitmaps of the streams (lm_words 32-bit
+// words in all).  Wavefront: per-match records, granule index, per-block depth fields, per-level arrays.
+WsLayout layout(int n_streams, uint64_t total_tiles, bool wave, const aceapex_info *wi, uint64_t lm_words) {
     WsLayout L{};
     size_t at = 0;
     L.head = at; at = up(at + sizeof(WsHead));
@@ -71,12 +72,14 @@ WsLayout layout(int n_streams, uint64_t total_tiles, bool wave, const aceapex_in
     L.status = at; at = up(at + sizeof(int32_t) * (size_t)std::max(n_streams, 1));
     L.descs = at; at = up(at + (n_streams > 1 ? sizeof(StreamDesc) * (size_t)n_streams : 0));
     L.flags = at; at = up(at + sizeof(uint32_t) * (size_t)(wave ? 0 : total_tiles));
+    L.litmap = at; at = up(at + sizeof(uint32_t) * (size_t)(wave ? 0 : lm_words));
     if (wave && wi) {
         const uint64_t nm = wi->n_match, nb = wi->n_blocks;
         const uint32_t gl = std::min<uint32_t>(wi->tile_log2, kGranuleLog2);
         const uint64_t ng = (wi->decoded_len + (1ull << gl) - 1) >> gl;
         const uint64_t nl = (uint64_t)wi->max_depth + 2;
         L.block_base = at; at = up(at + 8 * (nb + 1));
+        L.bdepth = at; at = up(at + 4 * (nb + 1));
         L.mdst = at; at = up(at + 8 * nm);
         L.msrc = at; at = up(at + 8 * nm);
         L.mlen = at; at = up(at + 4 * nm);
@@ -97,6 +100,7 @@ WsLayout layout(int n_streams, uint64_t total_tiles, bool wave, const aceapex_in
 WaveBufs wave_bufs(uint8_t *ws, const WsLayout &L) {
     WaveBufs w;
     w.block_base = (unsigned long long *)(ws + L.block_base);
+    w.bdepth = (uint32_t *)(ws + L.bdepth);
     w.mdst = (unsigned long long *)(ws + L.mdst);
     w.msrc = (unsigned long long *)(ws + L.msrc);
     w.mlen = (uint32_t *)(ws + L.mlen);
@@ -112,6 +116,11 @@ WaveBufs wave_bufs(uint8_t *ws, const WsLayout &L) {
     return w;
 }
 
+// Workspace of one stream decoded alone.
+WsLayout layout_one(const aceapex_info &I, bool wave) {
+    return layout(1, I.n_tiles, wave, &I, wave ? 0 : litmap_words(I.decoded_len));
+}
+
 StreamDesc make_desc(const void *comp, void *out, const aceapex_info &I, uint64_t tile_base) {
     StreamDesc d{};
     d.comp = (const uint8_t *)comp;
@@ -125,6 +134,7 @@ StreamDesc make_desc(const void *comp, void *out, const aceapex_info &I, uint64_
     d.n_tiles = I.n_tiles;
     d.tile_off = 0;
     d.state = nullptr;
+    d.litmap = nullptr;
     d.flags = kDescLast;
     d.block_log2 = I.block_log2;
     d.tile_log2 = I.tile_log2;
@@ -154,7 +164,7 @@ struct DevPool {
 struct Context {
     std::mutex mu;
     std::map<int, DevPool> pools;
-    LaunchCfg cfg{0, 256, 4, 0, 2, 3};
+    LaunchCfg cfg{0, 4, 0, 2};
     bool force_wave = false;
     unsigned long long wait_ns = 4000000000ull;  // bounded device waits give up after 4 s
     unsigned long long withhold = ~0ull;
@@ -200,7 +210,12 @@ int pool_reserve(DevPool &p, size_t bytes, cudaStream_t stream) {
     return kOK;
 }
 
-bool use_wave(const aceapex_info &I) { return I.max_depth > 1 || ctx().force_wave; }
+// The one-pass kernel takes streams whose matches all have depth <= 1, with tiles of at most 4 KiB and at
+// most ~4 GiB of output (its positions are 32-bit); every other stream takes the wavefront path.
+bool one_pass_fits(const aceapex_info &I) {
+    return I.max_depth <= 1 && I.tile_log2 <= (uint32_t)kOnePassMaxTileLog2 && I.decoded_len <= kOnePassMaxN;
+}
+bool use_wave(const aceapex_info &I) { return !one_pass_fits(I) || ctx().force_wave; }
 
 // Enqueue the decode of one stream into workspace ws (layout L); the status goes to status_out.
 int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, const WsLayout &L,
@@ -209,6 +224,7 @@ int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws,
     cfg.num_sms = num_sms;
     LaunchArgs a{};
     a.one = make_desc(comp, out, I, 0);
+    a.one.litmap = (uint32_t *)(ws + L.litmap);
     a.n_streams = 1;
     a.total_tiles = I.n_tiles;
     a.wait_ns = ctx().wait_ns;
@@ -235,6 +251,10 @@ bool check_ptrs(const void *comp, size_t comp_len, const void *out, size_t out_l
 // Host helpers of the serving engine (serve.cpp); init_state is defined with the kernels (decode.cu).
 namespace aceapex_host {
 int init_state(aceapex::StreamState *st, cudaStream_t stream);
+bool one_pass_stream(const aceapex_info &I) {
+    std::lock_guard<std::mutex> g(ctx().mu);
+    return !use_wave(I);
+}
 LaunchCfg launch_cfg() {
     std::lock_guard<std::mutex> g(ctx().mu);
     return ctx().cfg;
@@ -251,7 +271,7 @@ int server_enqueue_whole(const void *comp, void *out, const aceapex_info &I, uin
     DevPool *p = nullptr;
     int rc = pool_for_device(&p);
     if (rc) return rc;
-    const WsLayout L = layout(1, I.n_tiles, use_wave(I), &I);
+    const WsLayout L = layout_one(I, use_wave(I));
     if (L.total > *ws_cap) {
         cudaStreamSynchronize(stream);
         cudaFree(*ws);
@@ -275,7 +295,7 @@ int aceapex_peek_header(const void *host_prefix, size_t len, aceapex_info *info)
 size_t aceapex_workspace_size(const aceapex_info *info) {
     if (!info) return 0;
     std::lock_guard<std::mutex> g(ctx().mu);
-    return layout(1, info->n_tiles, use_wave(*info), info).total;
+    return layout_one(*info, use_wave(*info)).total;
 }
 
 int aceapex_decode(const void *comp, size_t comp_len, void *out, size_t out_len, void *stream_) {
@@ -299,7 +319,7 @@ int aceapex_decode(const void *comp, size_t comp_len, void *out, size_t out_len,
     S.one_pass = !use_wave(I);
     if (I.decoded_len == 0) return (I.n_blocks || I.n_match || I.n_seq || I.max_depth) ? kErrFormat : kOK;
     const bool wave = use_wave(I);
-    const WsLayout L = layout(1, I.n_tiles, wave, &I);
+    const WsLayout L = layout_one(I, wave);
     rc = pool_reserve(*p, L.total, stream);
     if (rc) return rc;
     int32_t *d_status = (int32_t *)(p->ws + L.status);
@@ -339,7 +359,7 @@ int aceapex_decode_async(const void *comp, size_t comp_len, void *out, size_t ou
     int rc = pool_for_device(&p);
     if (rc) return rc;
     if (info->decoded_len == 0) return cuda_fail(cudaMemsetAsync(d_status, 0, 4, stream));
-    const WsLayout L = layout(1, info->n_tiles, use_wave(*info), info);
+    const WsLayout L = layout_one(*info, use_wave(*info));
     if (!d_ws || ws_len < L.total) return kErrNomem;
     return enqueue_one(comp, out, *info, (uint8_t *)d_ws, L, d_status, p->num_sms, stream);
 }
@@ -408,7 +428,8 @@ int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *com
     rc = read_headers(n, valid.data(), hdr, stream);
     if (rc) { delete P; return rc; }
     std::vector<StreamDesc> descs;
-    uint64_t tiles = 0;
+    std::vector<uint64_t> lm_at;  // word offset of each one-pass stream's literal bitmap
+    uint64_t tiles = 0, lm_words = 0;
     size_t wave_need = 0;
     for (int i = 0; i < n; i++) {
         if (P->arg_status[i]) continue;
@@ -420,19 +441,23 @@ int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *com
         if (I.decoded_len == 0) continue;  // nothing to do, status 0
         if (use_wave(I)) {
             P->wave_idx.push_back(i);
-            wave_need = std::max(wave_need, layout(1, I.n_tiles, true, &I).total);
+            wave_need = std::max(wave_need, layout_one(I, true).total);
         } else {
             P->flat_idx.push_back(i);
             P->flat_args.max_tile_log2 = std::max(P->flat_args.max_tile_log2, I.tile_log2);
             P->flat_args.max_n = std::max<unsigned long long>(P->flat_args.max_n, I.decoded_len);
             descs.push_back(make_desc(comps[i], outs[i], I, tiles));
             tiles += I.n_tiles;
+            lm_at.push_back(lm_words);
+            lm_words += litmap_words(I.decoded_len);
         }
     }
     const int nf = (int)P->flat_idx.size();
-    P->flat_L = layout(std::max(nf, 2), tiles, false, nullptr);  // >= 2: the descriptor table always lives in memory
+    // >= 2 streams: the descriptor table always lives in memory
+    P->flat_L = layout(std::max(nf, 2), tiles, false, nullptr, lm_words);
     if (nf > 0) {
         if (cudaMalloc((void **)&P->ws, P->flat_L.total) != cudaSuccess) { cudaGetLastError(); delete P; return kErrNomem; }
+        for (int k = 0; k < nf; k++) descs[k].litmap = (uint32_t *)(P->ws + P->flat_L.litmap) + lm_at[k];
         cudaMemsetAsync(P->ws, 0, P->flat_L.total, stream);
         cudaMemcpyAsync(P->ws + P->flat_L.descs, descs.data(), sizeof(StreamDesc) * nf, cudaMemcpyHostToDevice, stream);
         P->flat_args.n_streams = nf;
@@ -472,7 +497,7 @@ static int plan_enqueue(aceapex_batch_plan *P, cudaStream_t stream) {
     for (size_t k = 0; k < P->wave_idx.size(); k++) {
         const int i = P->wave_idx[k];
         const aceapex_info &I = P->info[i];
-        const WsLayout L = layout(1, I.n_tiles, true, &I);
+        const WsLayout L = layout_one(I, true);
         int rc = enqueue_one(P->comps[i], P->outs[i], I, P->wave_ws, L, P->wave_status + k, P->num_sms, stream);
         if (rc) return rc;
     }
@@ -548,30 +573,19 @@ int aceapex_decode_batch(int n, const void *const *comps, const size_t *comp_len
 }
 
 // ------------------------------------------------------------------------------------------ config, stats
-int aceapex_set_launch_config(int threads, int ctas_per_sm, int spt) {
-    const bool ok = (threads == 128 && (spt == 4 || spt == 8)) || (threads == 256 && (spt == 2 || spt == 4 || spt == 8)) ||
-                    (threads == 512 && (spt == 2 || spt == 4));
-    if (!ok || ctas_per_sm < 0) return kErrArg;
+int aceapex_set_launch_config(int warps_per_cta, int ctas_per_sm) {
+    if ((warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8) || ctas_per_sm < 0) return kErrArg;
     std::lock_guard<std::mutex> g(ctx().mu);
-    ctx().cfg.threads = threads;
+    ctx().cfg.warps = warps_per_cta;
     ctx().cfg.ctas_per_sm = ctas_per_sm;
-    ctx().cfg.spt = spt;
     return kOK;
 }
 
-int aceapex_get_launch_config(int *threads, int *ctas_per_sm, int *spt) {
-    if (!threads || !ctas_per_sm || !spt) return kErrArg;
+int aceapex_get_launch_config(int *warps_per_cta, int *ctas_per_sm) {
+    if (!warps_per_cta || !ctas_per_sm) return kErrArg;
     std::lock_guard<std::mutex> g(ctx().mu);
-    *threads = ctx().cfg.threads;
+    *warps_per_cta = ctx().cfg.warps;
     *ctas_per_sm = ctx().cfg.ctas_per_sm;
-    *spt = ctx().cfg.spt;
-    return kOK;
-}
-
-int aceapex_set_one_pass_kernel(int kind) {
-    if (kind < 0 || kind > 4) return kErrArg;
-    std::lock_guard<std::mutex> g(ctx().mu);
-    ctx().cfg.kernel = kind;
     return kOK;
 }
 
@@ -658,7 +672,7 @@ int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t
     if (!rc) rc = grow(&p->hd_out, &p->hd_out_cap, out_len);
     if (rc) return rc;
     const bool wave = use_wave(I);
-    const WsLayout L = layout(1, I.n_tiles, wave, &I);
+    const WsLayout L = layout_one(I, wave);
     rc = pool_reserve(*p, L.total, stream);
     if (rc) return rc;
     aceapex_stats &S = ctx().stats;
@@ -711,6 +725,7 @@ int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t
             a.one.n_tiles = t_beg[k + 1] - t_beg[k];
             a.one.tile_off = t_beg[k];
             a.one.state = p->hd_state;
+            a.one.litmap = (uint32_t *)(p->ws + L.litmap);
             a.one.flags = k + 1 == ns ? kDescLast : 0u;
             a.n_streams = 1;
             a.total_tiles = a.one.n_tiles;

@@ -1,31 +1,29 @@
 // ACEAPEX decode kernels for sm_103a and their host-side launch sequences.
 //
 // One-pass path (every match has depth <= 1, i.e. reads only literal bytes: chain flattening, §3.3):
-//   k_flat -- persistent CTAs take tiles from a global ticket queue (one queue over all the streams of a
-//   batch).  Phase A parses the tile and writes its literal bytes, then publishes a per-tile flag.  Phase B
-//   waits (bounded) until every earlier tile of the same stream has published, re-parses the tile (its
-//   varints are still in L2) and copies its matches from absolute offsets (§3.1).  Tickets are handed out
-//   in order and phase A never waits, so the wait always ends; no per-match metadata reaches HBM.
+//   k_flat (onepass.cuh) -- persistent warps take tiles from a global ticket queue (one queue over all the
+//   streams of a batch).  Pass A parses the tile, writes its literal bytes and literal bits and publishes a
+//   per-tile flag; pass B copies its matches from absolute offsets (§3.1) once the tiles they read have
+//   published.  Tickets are handed out in order and pass A never waits, so every wait ends; no per-match
+//   metadata reaches HBM.
 //
 // Wavefront path (§7.1, any depth): k_parse writes the literals and one record (destination, source,
-//   length) per match plus a granule index that finds the writers of any byte range; k_depth computes each
-//   match's depth = 1 + the largest depth among the matches that wrote its source (a ticketed dataflow
-//   over match indices, whose dependencies always point to smaller indices); k_hist/k_levels/k_scatter
-//   bucket the matches into per-level queues; k_wave, one cooperative persistent launch, drains level 1,
-//   2, ... with a bounded grid barrier between levels, instead of one kernel launch per level as in the
-//   paper's H100 design.
+//   length) per match plus a granule index that finds the writers of any byte range; k_flow_w (default)
+//   copies each match as soon as the matches that wrote its source have finished, computing its depth on
+//   the way; the alternatives compute every depth first (k_depth) and then either copy with them (the
+//   per-thread dataflow) or bucket the matches into per-level queues (k_hist/k_levels/k_scatter_w) that
+//   one cooperative persistent launch (k_wave_w) drains level by level with a bounded grid barrier in
+//   between, instead of one kernel launch per level as in the paper's H100 design.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "decode.h"
 #include "tile.cuh"
-#include "flat2.cuh"
-#include "flat3.cuh"
-#include "flat4.cuh"
-#include "flat5.cuh"
+#include "onepass.cuh"
 #include "wave.cuh"
 
 namespace aceapex {
@@ -57,7 +55,9 @@ __global__ void k_finalize(StreamState *sst, const StreamDesc *descs, LaunchArgs
     if (i >= a.n_streams) return;
     const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[i];
     StreamState &st = sd.state ? *sd.state : sst[i];
-    if ((sd.flags & kDescLast) && st.err_key == ~0ull &&
+    // the header totals are checked when every tile ran to its end (no error, or only depth errors)
+    const bool complete = st.err_key == ~0ull || (st.err_key >> 4) == kOrderDepth;
+    if ((sd.flags & kDescLast) && complete &&
         (st.seq_sum != sd.n_seq || st.match_sum != sd.n_match || st.depth_max != sd.max_depth))
         st.err_key = (kOrderTotals << 4) | (unsigned long long)(-kErrFormat);
     st.status = st.err_key == ~0ull ? 0 : -(int)(st.err_key & 15);
@@ -65,93 +65,13 @@ __global__ void k_finalize(StreamState *sst, const StreamDesc *descs, LaunchArgs
 }
 
 
-// ------------------------------------------------------------------------------------------ one-pass kernel
-template <int NT, int SPT>
-__global__ void __launch_bounds__(NT) k_flat(WsHead *head, StreamState *sst, uint32_t *flags, const StreamDesc *descs,
-                                             LaunchArgs a) {
-    __shared__ TileSmem<NT, SPT> sm;
-    __shared__ unsigned long long s_t;
-    __shared__ int s_si;
-    const uint32_t epoch = head->epoch;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_t = atomicAdd(&head->ticket, 1ull);
-            s_si = (s_t < a.total_tiles) ? (a.n_streams == 1 ? 0 : find_stream(descs, a.n_streams, s_t)) : 0;
-        }
-        __syncthreads();
-        const unsigned long long t = s_t;
-        if (t >= a.total_tiles) break;
-        const int si = s_si;
-        const StreamDesc &sd = a.n_streams == 1 ? a.one : descs[si];
-        StreamState *st = sd.state ? sd.state : &sst[si];
-        if (threadIdx.x == 0) {
-            const uint64_t lt = t - sd.tile_base + sd.tile_off;
-            const uint32_t sh = sd.block_log2 - sd.tile_log2;
-            sm.err = 0; sm.verr = 0;
-            // a stream that already failed is skipped (its flags are still published below)
-            sm.err = *(volatile int *)&st->status ? 1 : tile_open(sm, sd, lt >> sh, (uint32_t)(lt & ((1ull << sh) - 1)), st);
-        }
-        __syncthreads();
-        // phase A: literals
-        if (!sm.err) {
-            tile_rewind(sm);
-            while (sm.seq < sm.seq_end) {
-                if (!chunk_parse(sm, false)) break;
-                chunk_literals(sm, sd.out);
-                __syncthreads();
-            }
-        }
-        // publish this tile's literals
-        __threadfence();
-        __syncthreads();
-        const int err_a = sm.err;  // negative: a format error of this tile; 1: the stream failed earlier
-        const unsigned long long order = t - sd.tile_base + sd.tile_off;
-        if (threadIdx.x == 0) {
-            if (err_a < 0) report(st, err_a, order);
-            if (t != a.withhold) st_release_u32(&flags[t], epoch);
-        }
-        // phase B: wait for the literals of every earlier tile of this stream, then copy the matches
-        if (!err_a) {
-            if (threadIdx.x < 32) {
-                unsigned long long f = ld_acquire_u64(&st->front);
-                if (f < sd.tile_base) f = sd.tile_base;
-                const uint64_t t0 = global_ns();
-                bool timed_out = false;
-                while (f < t) {
-                    const unsigned long long k = f + threadIdx.x;
-                    const bool done = k >= t || ld_acquire_u32(&flags[k]) == epoch;
-                    const unsigned ball = __ballot_sync(0xffffffffu, done);
-                    if (ball == 0xffffffffu) { f += 32; continue; }
-                    f += __ffs(~ball) - 1;
-                    if (global_ns() - t0 > a.wait_ns) { timed_out = true; break; }
-                    __nanosleep(64);
-                }
-                if (threadIdx.x == 0) {
-                    if (timed_out) { report(st, kErrTimeout, kOrderTimeout); sm.err = kErrTimeout; }
-                    else atomicMax(&st->front, t < f ? t : f);
-                }
-            }
-            __syncthreads();
-            if (!sm.err) {
-                tile_rewind(sm);
-                while (sm.seq < sm.seq_end) {
-                    if (!chunk_parse(sm, true)) break;
-                    chunk_matches(sm, sd.out);
-                    __syncthreads();
-                }
-                if (threadIdx.x == 0 && sm.err) report(st, sm.err, order);
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------------------------------------ wavefront path
 constexpr int kNT = 256, kSPT = 4;
 
 // Prefix sum of the blocks' match counts (one CTA); block_base[n_blocks] = total, which must equal the
 // header's n_match (the record arrays are sized from it).
-__global__ void __launch_bounds__(kNT) k_match_base(StreamState *sst, LaunchArgs a, unsigned long long *block_base) {
+__global__ void __launch_bounds__(kNT) k_match_base(StreamState *sst, LaunchArgs a, unsigned long long *block_base,
+                                                    uint32_t *bdepth) {
     __shared__ ScanSmem<kNT> scan;
     __shared__ unsigned int s_depth;
     const StreamDesc &sd = a.one;
@@ -165,7 +85,9 @@ __global__ void __launch_bounds__(kNT) k_match_base(StreamState *sst, LaunchArgs
             const uint64_t boff = ld64(sd.comp + kStreamHeader + 8 * b);
             if ((boff & 15) == 0 && boff + kBlockHeader <= sd.comp_len) {
                 nm = ld32(sd.comp + boff + 4);
-                atomicMax(&s_depth, ld32(sd.comp + boff + 24));
+                const uint32_t bd = ld32(sd.comp + boff + 24);
+                atomicMax(&s_depth, bd);
+                bdepth[b] = bd;
             } else {
                 report(&sst[0], kErrFormat, b << (sd.block_log2 - sd.tile_log2));
             }
@@ -303,7 +225,9 @@ __global__ void __launch_bounds__(kNT) k_depth(WsHead *head, StreamState *sst, L
                 }
                 if (!(w < m && wb.mdst[w] < send)) {
                     uint32_t dep = mx + 1;
-                    if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
+                    // a match deeper than its block's max_depth field: the stream understates its depth
+                    if (L && dep > wb.bdepth[d >> sd.block_log2]) report_depth(&sst[0]);
+                    if (dep > cap) dep = cap;
                     if (COPY) {
                         if (L) thread_copy(sd.out, d, s, L);
                         __threadfence();
@@ -359,44 +283,6 @@ __global__ void __launch_bounds__(kNT) k_levels(WsHead *head, LaunchArgs a, Wave
         run += tot;
     }
     if (threadIdx.x == 0) { wb.lvl[nl] = (uint32_t)run; head->n_levels = head->depth_seen; }
-}
-
-__global__ void __launch_bounds__(kNT) k_scatter(LaunchArgs a, WaveBufs wb) {
-    const uint64_t n = a.one.n_match;
-    for (uint64_t m = (uint64_t)blockIdx.x * kNT + threadIdx.x; m < n; m += (uint64_t)gridDim.x * kNT) {
-        const uint32_t d = wb.depth[m];
-        if (d > a.one.max_depth) continue;
-        const unsigned peers = __match_any_sync(__activemask(), d);
-        const int leader = __ffs(peers) - 1;
-        const int rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1));
-        uint32_t base = 0;
-        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&wb.cursor[d], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        wb.queue[base + rank] = (uint32_t)m;
-    }
-}
-
-// Drain the per-level queues, level 1 first; one warp copies one match, lanes over 32-byte strides,
-// out[d+k] = out[s + (k mod (d-s))] so that a self-overlapping copy never reads its own output.
-__global__ void __launch_bounds__(kNT) k_wave(WsHead *head, StreamState *sst, LaunchArgs a, WaveBufs wb) {
-    if (*(volatile int *)&sst[0].status) return;  // uniform: the status is final before this launch
-    const uint32_t nlev = head->depth_seen;
-    const uint64_t t0 = global_ns();
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t warp = ((uint64_t)blockIdx.x * kNT + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * kNT) >> 5;
-    uint8_t *out = a.one.out;
-    for (uint32_t k = 1; k <= nlev; k++) {
-        const uint32_t beg = wb.lvl[k], end = wb.lvl[k + 1];
-        for (uint64_t i = beg + warp; i < end; i += nwarps) {
-            const uint32_t m = wb.queue[i];
-            if (m >= a.one.n_match) continue;
-            const uint64_t d = wb.mdst[m], s = wb.msrc[m], L = wb.mlen[m], p = d - s;
-            if (s >= d || d + L > a.one.N) continue;  // never true for records k_parse checked
-            for (uint64_t j = lane; j < L; j += 32) out[d + j] = ld_out(out + s + (j < p ? j : j % p));
-        }
-        if (k < nlev && !grid_barrier(head, &sst[0], t0, a.wait_ns)) return;
-    }
 }
 
 // ------------------------------------------------------------------------------------------ host side
@@ -459,93 +345,28 @@ int prof_collect(double *ms, unsigned long long *launches) {
 
 #define PROF(id, ...) do { prof_mark(id, true, stream); __VA_ARGS__; prof_mark(id, false, stream); } while (0)
 
-template <int NT, int SPT>
-static cudaError_t launch_flat_t(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags,
+// The one-pass kernel with `warps` warps per CTA (2, 4 or 8): persistent grid of as many CTAs per SM as
+// fit (or cfg.ctas_per_sm), at most one warp per tile.
+template <int WARPS>
+static cudaError_t launch_k_flat(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags,
                                  const StreamDesc *descs, const LaunchArgs &a, cudaStream_t stream) {
-    // the staged kernels keep positions and tile indices in 32 bits
-    const bool narrow = a.max_n > 0 && a.max_n <= kF4MaxN && a.total_tiles < (1ull << 31);
-    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && cfg.kernel == 4 && narrow) {
-        // one warp per tile, staged sections, 128 sequences per warp step
-        const size_t dyn = sizeof(F5Warp) * kF5Warps;
-        static bool attr5 = false;
-        if (!attr5) {
-            cudaError_t e = cudaFuncSetAttribute(k_flat5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-            if (e != cudaSuccess) return e;
-            attr5 = true;
-        }
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat5, 32 * kF5Warps, dyn);
+    const size_t dyn = sizeof(F4Warp) * WARPS;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_flat<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
-        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
-        if (occ < 1) occ = 1;
-        uint64_t grid = (uint64_t)occ * cfg.num_sms;
-        const uint64_t need = (a.total_tiles + kF5Warps - 1) / kF5Warps;
-        if (grid > need) grid = need;
-        if (grid < 1) grid = 1;
-        PROF(kKFlat, k_flat5<<<(unsigned)grid, 32 * kF5Warps, dyn, stream>>>(head, sst, flags, descs, a));
-        return cudaGetLastError();
-    }
-    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && (cfg.kernel == 3 || cfg.kernel == 4) && narrow) {
-        // one warp per tile, staged sections
-        const size_t dyn = sizeof(F4Warp) * kF4Warps;
-        static bool attr4 = false;
-        if (!attr4) {
-            cudaError_t e = cudaFuncSetAttribute(k_flat4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-            if (e != cudaSuccess) return e;
-            attr4 = true;
-        }
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat4, 32 * kF4Warps, dyn);
-        if (e != cudaSuccess) return e;
-        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
-        if (occ < 1) occ = 1;
-        uint64_t grid = (uint64_t)occ * cfg.num_sms;
-        const uint64_t need = (a.total_tiles + kF4Warps - 1) / kF4Warps;
-        if (grid > need) grid = need;
-        if (grid < 1) grid = 1;
-        PROF(kKFlat, k_flat4<<<(unsigned)grid, 32 * kF4Warps, dyn, stream>>>(head, sst, flags, descs, a));
-        return cudaGetLastError();
-    }
-    if (a.max_tile_log2 <= (unsigned)kWarpImgLog2 && (cfg.kernel == 0 || cfg.kernel == 3 || cfg.kernel == 4)) {
-        // one warp per tile
-        const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;
-        static bool attr3 = false;
-        if (!attr3) {
-            cudaError_t e = cudaFuncSetAttribute(k_flat3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-            if (e != cudaSuccess) return e;
-            attr3 = true;
-        }
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat3, 32 * kWarpsPerCta, dyn);
-        if (e != cudaSuccess) return e;
-        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
-        if (occ < 1) occ = 1;
-        uint64_t grid = (uint64_t)occ * cfg.num_sms;
-        const uint64_t need = (a.total_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
-        if (grid > need) grid = need;
-        if (grid < 1) grid = 1;
-        PROF(kKFlat, k_flat3<<<(unsigned)grid, 32 * kWarpsPerCta, dyn, stream>>>(head, sst, flags, descs, a));
-        return cudaGetLastError();
-    }
-    const bool image = a.max_tile_log2 <= (unsigned)kImgLog2 && cfg.kernel != 2;
-    const size_t dyn = image ? sizeof(FlatSmem<NT, SPT>) : 0;
-    static bool attr_set = false;
-    if (image && !attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_flat2<NT, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr = true;
     }
     int occ = 0;
-    cudaError_t e = image ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat2<NT, SPT>, NT, dyn)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat<NT, SPT>, NT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flat<WARPS>, 32 * WARPS, dyn);
     if (e != cudaSuccess) return e;
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
     if (occ < 1) occ = 1;
     uint64_t grid = (uint64_t)occ * cfg.num_sms;
-    if (grid > a.total_tiles) grid = a.total_tiles;
+    const uint64_t need = (a.total_tiles + WARPS - 1) / WARPS;
+    if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    if (image) PROF(kKFlat, k_flat2<NT, SPT><<<(unsigned)grid, NT, dyn, stream>>>(head, sst, flags, descs, a));
-    else PROF(kKFlat, k_flat<NT, SPT><<<(unsigned)grid, NT, 0, stream>>>(head, sst, flags, descs, a));
+    PROF(kKFlat, k_flat<WARPS><<<(unsigned)grid, 32 * WARPS, dyn, stream>>>(head, sst, flags, descs, a));
     return cudaGetLastError();
 }
 
@@ -556,12 +377,13 @@ cudaError_t launch_flat(const LaunchCfg &cfg, WsHead *head, StreamState *sst, ui
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.total_tiles > 0) {
-#define ACEAPEX_FLAT(NT_, SPT_) \
-    if (cfg.threads == NT_ && cfg.spt == SPT_) e = launch_flat_t<NT_, SPT_>(cfg, head, sst, flags, descs, a, stream); else
-        ACEAPEX_FLAT(128, 4) ACEAPEX_FLAT(128, 8) ACEAPEX_FLAT(256, 2) ACEAPEX_FLAT(256, 4) ACEAPEX_FLAT(256, 8)
-        ACEAPEX_FLAT(512, 2) ACEAPEX_FLAT(512, 4)
-        e = launch_flat_t<256, 4>(cfg, head, sst, flags, descs, a, stream);
-#undef ACEAPEX_FLAT
+        // the one-pass kernel keeps positions in 32 bits and needs tiles of at most 4 KiB; the host sends
+        // every other stream down the wavefront path
+        if (a.max_tile_log2 > (unsigned)kWarpImgLog2 || a.max_n > kF4MaxN || a.total_tiles >= (1ull << 31))
+            return cudaErrorInvalidValue;
+        e = cfg.warps == 2 ? launch_k_flat<2>(cfg, head, sst, flags, descs, a, stream)
+          : cfg.warps == 8 ? launch_k_flat<8>(cfg, head, sst, flags, descs, a, stream)
+                           : launch_k_flat<4>(cfg, head, sst, flags, descs, a, stream);
         if (e != cudaSuccess) return e;
     }
     PROF(kKFinalize, k_finalize<<<(ns + 255) / 256, 256, 0, stream>>>(sst, descs, a, status_out));
@@ -576,7 +398,7 @@ cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, co
     const StreamDesc &sd = a.one;
     if (sd.N > 0) {
         cudaMemsetAsync(wb.hist, 0, sizeof(uint32_t) * (sd.max_depth + 2), stream);
-        PROF(kKMatchBase, k_match_base<<<1, kNT, 0, stream>>>(sst, a, wb.block_base));
+        PROF(kKMatchBase, k_match_base<<<1, kNT, 0, stream>>>(sst, a, wb.block_base, wb.bdepth));
         if (sd.tile_log2 <= (uint32_t)kWarpImgLog2) {
             const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;
             static bool attr = false;
@@ -659,16 +481,17 @@ int init_state(aceapex::StreamState *st, cudaStream_t stream) {
 using namespace aceapex;
 namespace {
 
-// Scratch of the one-pass decode: launch head | stream state | status | per-tile flags.
-constexpr size_t kNoAllocBytes = 1u << 20;
+// Scratch of the one-pass decode: launch head | stream state | per-tile flags | literal bitmap (one bit per
+// output byte).  16 MiB: streams of up to ~127 MiB of output at 4 KiB tiles.
+constexpr size_t kNoAllocBytes = 16u << 20;
 constexpr size_t kNoAllocFlags = 1024;  // byte offset of the flags region
-constexpr uint64_t kNoAllocMaxTiles = (kNoAllocBytes - kNoAllocFlags) / sizeof(uint32_t);
 static_assert(sizeof(WsHead) <= 512 && sizeof(StreamState) <= 256, "no-alloc scratch layout");
 __device__ __align__(256) static uint8_t g_noalloc_scratch[kNoAllocBytes];
 
 // In host code the array's name is only a stand-in: the device address comes from cudaGetSymbolAddress,
-// looked up once per device (with that device current) and kept here.
+// looked up once per device (with that device current, under a lock) and kept here.
 constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kMaxDevices];
 int g_noalloc_sms[kMaxDevices];
 
@@ -680,33 +503,44 @@ extern "C" int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *o
     if (!comp || comp_len < kStreamHeader || ((uintptr_t)comp & 15) || (!out && out_len) || !info || !d_status)
         return kErrArg;
     if (info->comp_len != comp_len || info->decoded_len != out_len) return kErrSize;
-    // only the one-pass kernel fits the fixed scratch: streams of depth <= 1, at most kNoAllocMaxTiles tiles
-    // of at most 4 KiB
-    if (info->max_depth > 1 || info->n_tiles > kNoAllocMaxTiles || info->tile_log2 > (uint32_t)kWarpImgLog2)
+    // only the one-pass kernel fits the fixed scratch: streams of depth <= 1 and tiles of at most 4 KiB whose
+    // flags and literal bitmap fit
+    const uint64_t flag_bytes = (4 * info->n_tiles + 255) & ~255ull;
+    if (info->max_depth > 1 || info->tile_log2 > (uint32_t)kWarpImgLog2 || info->decoded_len > kF4MaxN ||
+        info->n_tiles > (kNoAllocBytes - kNoAllocFlags) / 4 ||
+        kNoAllocFlags + flag_bytes + 4 * litmap_words(info->decoded_len) > kNoAllocBytes)
         return kErrNomem;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { cudaGetLastError(); return kErrCuda; }
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return kErrCuda; }
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return kErrCuda;
+    void *addr = nullptr;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return kErrCuda; }
+            int n = 0;
+            if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                return kErrCuda;
+            }
+            g_noalloc_sms[dev] = n;
+            g_noalloc_addr[dev] = p;
         }
-        g_noalloc_sms[dev] = sms;
-        g_noalloc_addr[dev] = p;
+        addr = g_noalloc_addr[dev];
+        sms = g_noalloc_sms[dev];
     }
-    uint8_t *base = (uint8_t *)g_noalloc_addr[dev];
+    uint8_t *base = (uint8_t *)addr;
     WsHead *head = (WsHead *)base;
     StreamState *sst = (StreamState *)(base + 512);
     uint32_t *flags = (uint32_t *)(base + kNoAllocFlags);
+    uint32_t *litmap = (uint32_t *)(base + kNoAllocFlags + flag_bytes);
     if (info->decoded_len == 0) return cudaMemsetAsync(d_status, 0, 4, stream) == cudaSuccess ? kOK : kErrCuda;
     LaunchArgs a{};
     StreamDesc &d = a.one;
     d.comp = (const uint8_t *)comp; d.out = (uint8_t *)out; d.comp_len = comp_len; d.N = info->decoded_len;
     d.n_blocks = info->n_blocks; d.n_seq = info->n_seq; d.n_match = info->n_match; d.tile_base = 0;
-    d.n_tiles = info->n_tiles; d.tile_off = 0; d.state = nullptr; d.block_log2 = info->block_log2;
+    d.n_tiles = info->n_tiles; d.tile_off = 0; d.state = nullptr; d.litmap = litmap; d.block_log2 = info->block_log2;
     d.tile_log2 = info->tile_log2; d.min_match = info->min_match; d.max_depth = info->max_depth; d.flags = kDescLast;
     a.n_streams = 1;
     a.total_tiles = info->n_tiles;
@@ -714,13 +548,15 @@ extern "C" int aceapex_decode_noalloc(const void *comp, size_t comp_len, void *o
     a.withhold = ~0ull;
     a.max_tile_log2 = info->tile_log2;
     a.phase = nullptr;
-    // k_reset zeroes the launch head and stream state of every call; the tile flags need no clearing:
-    // they hold the epoch of the call that last published them, and each call runs with a new epoch
+    // k_reset zeroes the launch head and stream state of every call; the tile flags need no clearing (they
+    // hold the epoch of the call that last published them, and each call runs with a new epoch), nor does
+    // the literal bitmap (every tile writes all of its bits before it publishes)
     k_reset<<<1, 256, 0, stream>>>(head, sst, nullptr, a);
-    const size_t dyn = sizeof(WarpSmem) * kWarpsPerCta;  // below the 48 KiB default: no attribute needed
-    const uint64_t need = (a.total_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
-    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)g_noalloc_sms[dev] * 6));
-    k_flat3<<<(unsigned)grid, 32 * kWarpsPerCta, dyn, stream>>>(head, sst, flags, nullptr, a);
+    const size_t dyn = sizeof(F4Warp) * kF4Warps;  // below the 48 KiB default: no attribute needed
+    static_assert(sizeof(F4Warp) * kF4Warps <= 48 * 1024, "no-alloc launch needs no shared-memory attribute");
+    const uint64_t need = (a.total_tiles + kF4Warps - 1) / kF4Warps;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sms * 4));
+    k_flat<kF4Warps><<<(unsigned)grid, 32 * kF4Warps, dyn, stream>>>(head, sst, flags, nullptr, a);
     k_finalize<<<1, 32, 0, stream>>>(sst, nullptr, a, d_status);
     return cudaGetLastError() == cudaSuccess ? kOK : kErrCuda;
 }

@@ -20,22 +20,18 @@ struct LaunchArgs {
 };
 constexpr int kPhases = 8;  // open, parse, literals, store+publish, wait, matches, store, tiles
 
-// Launch shape of the one-pass kernel.
+// Launch shape and schedulers.
 struct LaunchCfg {
     int num_sms;
-    int threads;      // 128, 256 or 512
-    int spt;          // sequences per thread per parse chunk
-    int ctas_per_sm;  // 0 = as many as fit
-    int wave_sched;   // deep streams: 0 dataflow (each match copied once its writers published), 1 level queues
-    int kernel;       // one-pass kernel: 0 warp per tile (tiles <= 4 KiB) else 1; 1 CTA per tile with a
-                      // 16 KiB image; 2 CTA per tile storing straight to HBM (comparison and testing);
-                      // 3 warp per tile with staged sections (tiles <= 4 KiB, streams < ~4 GiB) else 0;
-                      // 4 the same with 128 sequences per warp step
+    int warps;        // one-pass kernel: warps per CTA (2, 4 or 8)
+    int ctas_per_sm;  // one-pass kernel: CTAs per SM (0 = as many as fit)
+    int wave_sched;   // deep streams: 0 per-match dataflow, 1 level queues, 2 warp dataflow (default)
 };
 
 // Device buffers of the wavefront path (carved from the workspace).
 struct WaveBufs {
     unsigned long long *block_base;  // n_blocks + 1 prefix sums of per-block match counts
+    uint32_t *bdepth;                // per block: its header's max_depth field
     unsigned long long *mdst, *msrc; // per match: absolute destination and source
     uint32_t *mlen, *depth, *queue;  // per match: length, depth, level-queue entry
     uint32_t *gidx;                  // per granule: first match ending after the granule start

@@ -15,6 +15,11 @@ __device__ __forceinline__ void report(StreamState *st, int code, unsigned long 
     atomicMin(&st->err_key, (order << 4) | (unsigned long long)(-code));
     atomicCAS(&st->status, 0, code);
 }
+// A match deeper than its block's max_depth field: recorded after every tile error and the header totals,
+// as the last check of a stream, without stopping the other tiles (their errors still come first).
+__device__ __forceinline__ void report_depth(StreamState *st) {
+    atomicMin(&st->err_key, (kOrderDepth << 4) | (unsigned long long)(-kErrDepth));
+}
 
 // ------------------------------------------------------------------------------------------ memory
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {

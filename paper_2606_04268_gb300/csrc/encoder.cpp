@@ -5,7 +5,13 @@
 // Parse rules (deterministic, so that a stream is a pure function of input and parameters):
 //   * every position q with q+4 <= N is hashed (4 bytes LE x 2654435761, top hash_bits) and chained;
 //     the first position of each hash value is also remembered;
-//   * candidates at p: up to chain_limit most recent chained positions, then the hash's first position;
+//   * with long_bits set, every position q with q+12 <= N is also chained under a hash of its 12 bytes
+//     (8-byte and 4-byte LE words times two odd constants, summed mod 2^64, top long_bits): a key that
+//     stays selective on small alphabets such as DNA bases, where 4-byte keys take few values; in flatten
+//     modes only literal positions (their own root) enter this chain, so that its candidates start on
+//     bytes a flattened match may point at;
+//   * candidates at p: up to long_chain most recent positions of the 12-byte chain, then up to chain_limit
+//     most recent positions of the 4-byte chain, then the 4-byte hash's first position;
 //   * a candidate's length is its common prefix with the input at p, cut at p's block end; in flatten
 //     modes it is also cut where the roots of its source bytes stop being consecutive, and the match then
 //     points at the first root (a self-overlapping candidate keeps its full length only when its source
@@ -18,6 +24,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <new>
@@ -40,6 +47,38 @@ struct alignas(64) Ring {
     uint32_t pos[kRing];
 };
 
+// A table of n elements of T, all set to v.  Large tables are placed on 2 MiB boundaries and the kernel is
+// asked to back them with huge pages: the parse reads them at random, and with small pages nearly every
+// access would also miss the TLB.
+template <typename T>
+struct Table {
+    T *p = nullptr;
+    size_t n = 0;
+    Table() = default;
+    Table(const Table &) = delete;
+    Table &operator=(const Table &) = delete;
+    ~Table() { free(p); }
+    bool init(size_t count, const T &v) {
+        free(p);
+        p = nullptr;
+        n = count;
+        const size_t bytes = count * sizeof(T), huge = (size_t)2 << 20;
+        void *q = nullptr;
+        if (bytes >= huge) {
+            if (posix_memalign(&q, huge, (bytes + huge - 1) / huge * huge) != 0) return false;
+            madvise(q, (bytes + huge - 1) / huge * huge, MADV_HUGEPAGE);  // a hint: failure changes nothing
+        } else {
+            q = malloc(bytes ? bytes : 1);
+            if (!q) return false;
+        }
+        p = (T *)q;
+        for (size_t i = 0; i < count; i++) p[i] = v;
+        return true;
+    }
+    T &operator[](size_t i) { return p[i]; }
+    const T &operator[](size_t i) const { return p[i]; }
+};
+
 struct Match {
     uint32_t d, s, L;
 };
@@ -50,6 +89,13 @@ inline uint32_t load32(const uint8_t *p) {
     return v;  // little-endian host assumed (x86-64, aarch64)
 }
 inline uint32_t hash4(const uint8_t *p, uint32_t bits) { return (load32(p) * 2654435761u) >> (32 - bits); }
+inline uint32_t hash12(const uint8_t *p, uint32_t bits) {
+    uint64_t lo;
+    memcpy(&lo, p, 8);
+    const uint64_t v = lo * 0x9E3779B97F4A7C15ull + (uint64_t)load32(p + 8) * 0xC2B2AE3D27D4EB4Full;
+    return (uint32_t)(v >> (64 - bits));
+}
+constexpr uint32_t kLongKey = 12, kLongMax = 16;
 
 // Common prefix of a[0..) and b[0..), at most lim bytes, 8 bytes at a time.
 inline uint32_t common_prefix(const uint8_t *a, const uint8_t *b, uint32_t lim) {
@@ -70,18 +116,19 @@ struct Parser {
     const uint8_t *in;
     uint32_t N;
     aceapex_enc_params P;
-    std::vector<Ring> ring;
-    std::vector<uint32_t> first, root, wdepth;
+    Table<Ring> ring;
+    Table<uint32_t> ring2;  // long-key chain: long_chain most recent positions per hash, most recent first
+    Table<uint32_t> first, root, wdepth;
     std::vector<Match> out;
 
     bool init() {
         try {
             Ring empty;
             for (uint32_t i = 0; i < kRing; i++) empty.pos[i] = kNone;
-            ring.assign(1u << P.hash_bits, empty);
-            first.assign(1u << P.hash_bits, kNone);
-            wdepth.assign(N, 0);
-            if (P.flatten) root.resize(N);
+            if (!ring.init((size_t)1 << P.hash_bits, empty) || !first.init((size_t)1 << P.hash_bits, kNone) ||
+                (P.long_bits && !ring2.init((size_t)P.long_chain << P.long_bits, kNone)) || !wdepth.init(N, 0) ||
+                (P.flatten && !root.init(N, 0)))
+                return false;
             out.reserve(N / 16 + 16);
         } catch (...) {
             return false;
@@ -94,19 +141,51 @@ struct Parser {
         return (P.flatten == 2 || (x >> bl) == (p >> bl)) ? root[x] : x;
     }
 
+    // The hash tables are far larger than the caches and every position is entered in order: while entering
+    // q, fetch the buckets of position q + 2 kAhead and the bytes (and roots) of the long-key candidates of
+    // q + kAhead, whose bucket was fetched kAhead positions ago, so that their misses overlap.
+    static constexpr uint32_t kAhead = 32;
+    void prefetch(uint32_t q) {
+        const uint32_t q2 = q + 2 * kAhead;
+        if ((uint64_t)q2 + kLongKey <= N) {
+            const uint32_t h = hash4(in + q2, P.hash_bits);
+            __builtin_prefetch(&ring[h], 1);
+            __builtin_prefetch(&first[h], 1);
+            if (P.long_bits) __builtin_prefetch(&ring2[(size_t)hash12(in + q2, P.long_bits) * P.long_chain], 1);
+        }
+        const uint32_t q1 = q + kAhead;
+        if ((uint64_t)q1 + kLongKey <= N) {
+            if (P.long_bits) {
+                const uint32_t *r2 = &ring2[(size_t)hash12(in + q1, P.long_bits) * P.long_chain];
+                for (uint32_t k = 0; k < P.long_chain && r2[k] != kNone; k++) {
+                    __builtin_prefetch(in + r2[k]);
+                    if (P.flatten) __builtin_prefetch(&root[r2[k]]);
+                }
+            }
+            const Ring &rg = ring[hash4(in + q1, P.hash_bits)];
+            for (uint32_t k = 0; k < P.chain_limit && rg.pos[k] != kNone; k++) __builtin_prefetch(in + rg.pos[k]);
+        }
+    }
+
     void insert(uint32_t q) {
+        prefetch(q);
         if ((uint64_t)q + 4 > N) return;
         const uint32_t h = hash4(in + q, P.hash_bits);
         Ring &r = ring[h];
         memmove(&r.pos[1], &r.pos[0], sizeof(uint32_t) * (kRing - 1));
         r.pos[0] = q;
         if (first[h] == kNone) first[h] = q;
+        if (P.long_bits && (uint64_t)q + kLongKey <= N && (!P.flatten || root[q] == q)) {
+            uint32_t *r2 = &ring2[(size_t)hash12(in + q, P.long_bits) * P.long_chain];
+            memmove(r2 + 1, r2, sizeof(uint32_t) * (P.long_chain - 1));
+            r2[0] = q;
+        }
     }
 
     void run() {
         const uint32_t mm = std::max(P.min_match, P.min_emit), cap = P.depth_cap, bl = P.block_log2;
         const bool flat = P.flatten != 0;
-        uint32_t cand[kRing + 1];
+        uint32_t cand[kLongMax + kRing + 1];
         uint32_t p = 0;
         while (p < N) {
             const uint32_t blk_end = (uint32_t)std::min<uint64_t>(((uint64_t)(p >> bl) + 1) << bl, N);
@@ -115,8 +194,12 @@ struct Parser {
             if (maxL >= mm && (uint64_t)p + 4 <= N) {
                 const uint32_t h = hash4(in + p, P.hash_bits);
                 uint32_t nc = 0;
+                if (P.long_bits && (uint64_t)p + kLongKey <= N) {
+                    const uint32_t *r2 = &ring2[(size_t)hash12(in + p, P.long_bits) * P.long_chain];
+                    for (uint32_t k = 0; k < P.long_chain && r2[k] != kNone; k++) cand[nc++] = r2[k];
+                }
                 const Ring &rg = ring[h];
-                while (nc < P.chain_limit && rg.pos[nc] != kNone) { cand[nc] = rg.pos[nc]; nc++; }
+                for (uint32_t k = 0; k < P.chain_limit && rg.pos[k] != kNone; k++) cand[nc++] = rg.pos[k];
                 if (P.use_first && first[h] != kNone) cand[nc++] = first[h];
                 for (uint32_t j = 0; j < nc; j++) __builtin_prefetch(in + cand[j]);
                 for (uint32_t j = 0; j < nc; j++) {
@@ -287,7 +370,8 @@ int64_t aceapex_encode(const void *in, size_t n, const aceapex_enc_params *param
     if (!P.hash_bits) P.hash_bits = 20;
     if (n >= 0xFFFFFFFFull || P.block_log2 < 2 || P.block_log2 > 24 || P.tile_log2 < 2 || P.tile_log2 > P.block_log2 ||
         P.min_match < 1 || P.min_match > 255 || P.flatten > 2 || P.chain_limit > kRing || P.hash_bits < 8 ||
-        P.hash_bits > 24)
+        P.hash_bits > 24 ||
+        (P.long_bits && (P.long_bits < 8 || P.long_bits > 28 || P.long_chain < 1 || P.long_chain > kLongMax)))
         return aceapex::kErrArg;
     Parser ps;
     ps.in = (const uint8_t *)in;
@@ -296,9 +380,11 @@ int64_t aceapex_encode(const void *in, size_t n, const aceapex_enc_params *param
     if (!ps.init()) return aceapex::kErrNomem;
     ps.run();
     // release the parse state before serializing
-    std::vector<Ring>().swap(ps.ring);
-    std::vector<uint32_t>().swap(ps.root);
-    std::vector<uint32_t>().swap(ps.wdepth);
+    ps.ring.init(0, Ring{});
+    ps.ring2.init(0, 0u);
+    ps.first.init(0, 0u);
+    ps.root.init(0, 0u);
+    ps.wdepth.init(0, 0u);
     return serialize(ps.in, n, ps.out, P, out);
 }
 

@@ -12,6 +12,8 @@ constexpr uint32_t kBlockHeader = 32;     // block header bytes (§2.1)
 constexpr uint32_t kSyncEntry = 20;       // sync-table entry bytes (§2.3)
 constexpr uint32_t kMinBlockLog2 = 2, kMaxBlockLog2 = 24;
 constexpr uint32_t kGranuleLog2 = 6;      // writer-index granule: 64 output bytes (or the tile, if smaller)
+constexpr uint32_t kOnePassMaxTileLog2 = 12;          // largest tile of the one-pass kernel (one warp per tile)
+constexpr unsigned long long kOnePassMaxN = 0xFFF00000ull;  // its positions are 32-bit: ~4 GiB of output
 
 // status codes (mirror aceapex_status)
 enum : int { kOK = 0, kErrArg = -1, kErrFormat = -2, kErrSize = -3, kErrOffset = -4, kErrTimeout = -5,
@@ -37,6 +39,7 @@ struct StreamDesc {
     uint64_t n_tiles;     // tiles of the stream decoded by this launch
     uint64_t tile_off;    // index (within the stream) of the first of them: earlier tiles are already decoded
     struct StreamState *state;  // persistent per-stream state (served requests), else the launch's own array
+    uint32_t *litmap;     // one-pass path: bit x set once output byte x is known to be a literal byte
     uint32_t block_log2, tile_log2, min_match, max_depth;
     uint32_t flags;       // bit 0: this launch completes the stream: check the header totals at the end
     uint32_t pad;
@@ -68,6 +71,9 @@ struct WsHead {
     unsigned int pad[7];
     unsigned long long phase[8];   // per-phase SM cycles of the one-pass kernel (profiling only)
 };
+
+// 32-bit words of a stream's literal bitmap (one bit per output byte, one spare word).
+inline uint64_t litmap_words(uint64_t N) { return (N + 31) / 32 + 1; }
 
 // Tiles of a stream: every block but the last has 2^(block_log2 - tile_log2) tiles.
 inline uint64_t stream_tiles(uint64_t N, uint32_t block_log2, uint32_t tile_log2) {

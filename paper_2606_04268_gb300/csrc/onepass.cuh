@@ -6,16 +6,19 @@
 //
 //   stage   lane 0 issues cp.async.bulk copies of the tile's ranges of cmd[], len[], off[] and lit[] (§3.2)
 //           into the warp's shared memory, completing on the warp's mbarrier; meanwhile the warp clears its
-//           image of the tile;
+//           image of the tile and the tile's literal bitmap;
 //   pass A  sequences are parsed 32 at a time from the staged bytes (lane k <- sequence k of the group:
 //           LEB128 values by a ballot over terminator bytes, output positions by shuffle scans, §3.2); each
 //           lane ORs the part of its literal run that falls in the tile into the zeroed image, a 16-byte piece
-//           at a time (five aligned word ORs per piece, no byte stores); the image goes to HBM with 16-byte
-//           stores and the tile's flag is published;
+//           at a time (five aligned word ORs per piece, no byte stores), and marks those bytes in the tile's
+//           literal bitmap (one bit per output byte); the image and the bitmap go to HBM and the tile's flag
+//           is published;
 //   pass B  the staged varints are parsed again with the absolute offsets (§3.1); each lane waits (bounded)
 //           until the tiles holding its match's source bytes have published their literals -- only those
-//           tiles, so no tile waits on the slowest of all earlier ones -- and ORs its match into the image,
-//           reading the source bytes from HBM (literal bytes); the image is stored again.
+//           tiles, so no tile waits on the slowest of all earlier ones -- checks that every source byte is
+//           a literal byte (a match that reads a match byte has depth >= 2, which the stream's
+//           max_depth <= 1 denies: ACEAPEX_ERR_DEPTH), and ORs its match into the image, reading the source
+//           bytes from HBM; the image is stored again.
 //
 // Pieces: a lane copies the first 16 bytes of its segment itself; the later pieces of longer segments are
 // dealt round-robin to all lanes (exclusive scan of the piece counts, binary search for the owner).  A
@@ -23,9 +26,10 @@
 // period boundaries: byte k of the match reads s + (k mod p).
 //
 // Sections that do not fit the stage, or a group whose bytes lie outside the staged ranges (possible only in
-// a malformed stream), are read from global memory instead, with the same results.
+// a malformed stream), are read from global memory instead, with the same results.  Positions are 32-bit:
+// streams of up to ~4 GiB of output (kF4MaxN).
 #pragma once
-#include "flat3.cuh"
+#include "warp_tile.cuh"
 
 namespace aceapex {
 
@@ -34,14 +38,19 @@ constexpr uint32_t kF4Stage = 5120;                           // staged section 
 constexpr uint32_t kF4Slack = 48;                             // readable bytes after the staged data
 constexpr uint32_t kF4LitCap = (1u << kWarpImgLog2) + 512;    // literal window staged per tile
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr unsigned long long kF4MaxN = 0xFFF00000ull;      // streams up to ~4 GiB: positions fit 32 bits
+constexpr unsigned long long kF4MaxN = kOnePassMaxN;       // streams up to ~4 GiB: positions fit 32 bits
+static_assert(kWarpImgLog2 == (int)kOnePassMaxTileLog2, "one warp per tile of at most 4 KiB");
+
+constexpr uint32_t kF4Img = (1u << kWarpImgLog2) + 32;       // image: alignment shift + tile + slack
+constexpr uint32_t kF4LbmWords = kF4Img / 32 + 4;
 
 struct alignas(16) F4Warp {
     WarpTile c;                                               // tile context, varint hand-off
     unsigned long long mbar;                                  // completion of the staging copies
     uint32_t pad_[2];
     alignas(16) uint8_t stage[kF4Stage + kF4Slack];
-    alignas(16) uint8_t img[(1u << kWarpImgLog2) + 32];
+    alignas(16) uint8_t img[kF4Img];
+    uint32_t lbm[kF4LbmWords];                                // bit i: image byte i is a literal byte
 };
 
 // ------------------------------------------------------------------------------------------ PTX helpers
@@ -235,8 +244,33 @@ __device__ __forceinline__ void f4_match_piece(uint32_t *imgw, uint32_t ib, cons
     }
 }
 
+// ------------------------------------------------------------------------------------------ literal bits
+// Mark image bytes [ib, ib + n) (n <= 32) as literal bytes.
+__device__ __forceinline__ void f4_mark(uint32_t *lbm, uint32_t ib, uint32_t n) {
+    const uint32_t q = ib >> 5, o = ib & 31u;
+    const unsigned long long m = (n >= 32 ? 0xFFFFFFFFull : ((1ull << n) - 1)) << o;
+    atomicOr(&lbm[q], (uint32_t)m);
+    if (m >> 32) atomicOr(&lbm[q + 1], (uint32_t)(m >> 32));
+}
+
+// Bits [a, b) (a < b) of a bit array all set: GLOB reads the array through L2 (written by other warps of
+// this launch), else from shared memory.
+template <bool GLOB>
+__device__ __forceinline__ bool f4_bits(const uint32_t *w, uint64_t a, uint64_t b) {
+    const uint64_t q0 = a >> 5, q1 = (b - 1) >> 5;
+    bool ok = true;
+    for (uint64_t q = q0; q <= q1 && ok; q++) {
+        const uint32_t lo = q == q0 ? (uint32_t)(a & 31u) : 0u, hi = q == q1 ? (uint32_t)((b - 1) & 31u) + 1 : 32u;
+        const uint32_t m = __funnelshift_lc(0xFFFFFFFFu, 0u, hi) & ~__funnelshift_lc(0xFFFFFFFFu, 0u, lo);
+        const uint32_t v = GLOB ? __ldcg(w + q) : w[q];
+        ok = (v & m) == m;
+    }
+    return ok;
+}
+
 // ------------------------------------------------------------------------------------------ kernel
-__global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamState *sst, uint32_t *flags,
+template <int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_flat(WsHead *head, StreamState *sst, uint32_t *flags,
                                                          const StreamDesc *descs, LaunchArgs a) {
     extern __shared__ uint4 dyn_smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -278,6 +312,11 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
         const uint8_t *sbase[4];
         uint32_t staged = 0;
         if (!err) {
+            // a block's header denies matches while having some (depth 1 > 0)
+            if (lane == 0 && (order & ((1ull << bsh) - 1)) == 0 && c.n_match > 0) {
+                const uint64_t boff = ld64(sd.comp + kStreamHeader + 8 * (order >> bsh));
+                if (ld32(sd.comp + boff + 24) == 0) report_depth(st);
+            }
             const uint32_t w = c.w;
             const uint32_t m_lo = c.e_seq < c.n_match ? c.e_seq : c.n_match;
             const uint32_t m_hi = c.seq_end < c.n_match ? c.seq_end : c.n_match;
@@ -310,6 +349,7 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
         }
         // clear the image while the copies run
         for (uint32_t g = lane; g < sizeof(W.img) / 16; g += 32) reinterpret_cast<uint4 *>(W.img)[g] = make_uint4(0, 0, 0, 0);
+        for (uint32_t g = lane; g < kF4LbmWords; g += 32) W.lbm[g] = 0;
         if (staged) {
             const uint64_t t0 = global_ns();
             bool ok = mbar_try_wait(&W.mbar, parity);
@@ -398,12 +438,14 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                     if (first) {
                         if (smem_src) or_piece_smem(wbase, imgw, ib, so, first);
                         else or_piece_glob<true>(imgw, ib, c.lit, src, first);
+                        f4_mark(W.lbm, ib, first);
                     }
                     if (__any_sync(kFull, len > 16)) {
                         const uint32_t second = len > 32 ? 16u : (len > 16 ? len - 16 : 0u);
                         if (second) {
                             if (smem_src) or_piece_smem(wbase, imgw, ib + 16, so + 16, second);
                             else or_piece_glob<true>(imgw, ib + 16, c.lit, src + 16, second);
+                            f4_mark(W.lbm, ib + 16, second);
                         }
                     }
                     // pieces from the third on: round-robin over the warp
@@ -428,6 +470,7 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                                 const uint32_t pl = (o_len - off) < 16 ? o_len - off : 16u;
                                 if (smem_src) or_piece_smem(wbase, imgw, o_ib + off, o_so + off, pl);
                                 else or_piece_glob<true>(imgw, o_ib + off, c.lit, o_src + off, pl);
+                                f4_mark(W.lbm, o_ib + off, pl);
                             }
                         }
                     }
@@ -501,6 +544,20 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                         __syncwarp();
                     }
                     WPHASE(4);
+                    // every source byte read must be a literal byte: this tile's part against the bits in
+                    // shared memory, earlier tiles' against the published bits in HBM
+                    if (len) {
+                        const uint64_t tile_abs = c.b0 + lo;
+                        const uint64_t ra = wrap ? s : (uint64_t)s + k0;
+                        const uint64_t rb = wrap ? (uint64_t)b0 + d : (uint64_t)s + k0 + len;
+                        const uint64_t rg = rb < tile_abs ? rb : tile_abs;
+                        bool lit = ra >= rg || f4_bits<true>(sd.litmap, ra, rg);
+                        if (lit && rb > tile_abs) {
+                            const uint64_t a2 = ra > tile_abs ? ra : tile_abs;
+                            lit = f4_bits<false>(W.lbm, a2 - tile_abs + ishift, rb - tile_abs + ishift);
+                        }
+                        if (!lit) report_depth(st);
+                    }
                     const uint32_t first = len < 16 ? len : 16u;
                     if (first) f4_match_piece(imgw, ib, sd.out, s, p, k0, first, wrap);
                     const uint32_t extra = len > 16 ? (len - 1) >> 4 : 0u;
@@ -552,6 +609,25 @@ __global__ void __launch_bounds__(32 * kF4Warps) k_flat4(WsHead *head, StreamSta
                 }
             }
             if (!matches) {
+                // the tile's literal bits (bit x: output byte x of the stream), published with the flag
+                const uint32_t nbits = hi - lo;
+                const unsigned long long tile_abs = c.b0 + lo;
+                if (sd.tile_log2 >= 5) {
+                    uint32_t *gw = sd.litmap + (tile_abs >> 5);
+                    const uint32_t nwd = (nbits + 31) >> 5;
+                    for (uint32_t w = lane; w < nwd; w += 32) {
+                        uint32_t v = __funnelshift_r(W.lbm[w], W.lbm[w + 1], ishift);
+                        if (w == nwd - 1 && (nbits & 31u)) v &= (1u << (nbits & 31u)) - 1u;
+                        gw[w] = v;
+                    }
+                } else if (lane == 0) {
+                    // tiles of 4, 8 or 16 bytes share a word with their neighbours
+                    const uint32_t m = (1u << nbits) - 1u, off = (uint32_t)(tile_abs & 31u);
+                    const uint32_t v = __funnelshift_r(W.lbm[0], W.lbm[1], ishift) & m;
+                    uint32_t *gw = sd.litmap + (tile_abs >> 5);
+                    atomicAnd(gw, ~(m << off));
+                    atomicOr(gw, v << off);
+                }
                 __threadfence();
                 __syncwarp();
                 if (lane == 0 && t != a.withhold) st_release_u32(&flags[t], epoch);

@@ -26,6 +26,7 @@ namespace aceapex_host {
 int server_enqueue_whole(const void *comp, void *out, const aceapex_info &I, uint8_t **ws, size_t *ws_cap,
                          int32_t *status_out, cudaStream_t stream);
 LaunchCfg launch_cfg();
+bool one_pass_stream(const aceapex_info &I);
 int num_sms();
 int init_state(StreamState *st, cudaStream_t stream);
 }  // namespace aceapex_host
@@ -37,7 +38,10 @@ struct Req {
     size_t comp_len = 0;
     aceapex_info info{};
     void *out = nullptr;
-    size_t bytes = 0;         // budget share: stream + output
+    bool whole = false;          // decoded whole by the wavefront path (else in slices by the one-pass kernel)
+    uint32_t *litmap = nullptr;  // one-pass requests: literal bitmap, allocated right after the output
+    size_t out_alloc = 0;     // output bytes (+ literal bitmap) allocated at admission
+    size_t bytes = 0;         // budget share: stream + output allocation
     uint64_t next_tile = 0;   // tiles [0, next_tile) are enqueued
     int slot = -1;
     int phase = 0;            // 0 queued, 1 admitted, 2 last slice enqueued, 3 released
@@ -130,7 +134,10 @@ int64_t aceapex_server_submit(aceapex_server *S, const void *comp, size_t comp_l
     r.comp = comp;
     r.comp_len = comp_len;
     r.info = *info;
-    r.bytes = comp_len + info->decoded_len;
+    const uint64_t N = info->decoded_len;
+    r.whole = !aceapex_host::one_pass_stream(*info);
+    r.out_alloc = r.whole ? (N ? N : 1) : align16(N) + 4 * litmap_words(N);
+    r.bytes = comp_len + r.out_alloc;
     if (r.bytes > S->budget) return kErrNomem;
     S->reqs.push_back(r);
     const int64_t id = (int64_t)S->reqs.size() - 1;
@@ -145,46 +152,59 @@ int aceapex_server_step(aceapex_server *S, void *stream_) {
     // ring entry of this step: wait for the step that used it before
     const int ring = (int)(S->step_no % kMaxStepsInFlight);
     if (S->step_no >= kMaxStepsInFlight && cudaEventSynchronize(S->ev[ring]) != cudaSuccess) return kErrCuda;
-    // 1. admission: arrival order, budget and slots
+    // 1. admission: arrival order, budget and slots.  A request is admitted only once its first work is
+    //    enqueued; if that fails it goes back to the head of the queue holding nothing, and step returns
+    //    the error (a later step retries it).
     while (!S->queue.empty()) {
-        Req &r = S->reqs[S->queue.front()];
+        const int64_t id = S->queue.front();
+        Req &r = S->reqs[id];
         int slot = -1;
         for (int k = 0; k < S->max_slots; k++) if (S->slot_owner[k] < 0) { slot = k; break; }
         if (slot < 0 || S->used + r.bytes > S->budget) break;
-        if (cudaMallocAsync(&r.out, r.info.decoded_len ? r.info.decoded_len : 1, stream) != cudaSuccess) {
+        if (cudaMallocAsync(&r.out, r.out_alloc, stream) != cudaSuccess) {
             cudaGetLastError();
+            r.out = nullptr;
             break;  // retry in a later step
         }
-        const int64_t id = S->queue.front();
+        r.litmap = r.whole ? nullptr : (uint32_t *)((uint8_t *)r.out + align16(r.info.decoded_len));
+        auto undo = [&](int rc) {
+            cudaFreeAsync(r.out, stream);
+            cudaGetLastError();
+            r.out = nullptr;
+            r.litmap = nullptr;
+            return rc;
+        };
+        if (aceapex_host::init_state(&S->d_state[slot], stream)) return undo(kErrCuda);
+        if (r.info.decoded_len > 0 && r.whole) {
+            // deep stream (or one the one-pass kernel does not take): decoded whole, here; its status is
+            // left in its workspace's state
+            const int rc = aceapex_host::server_enqueue_whole(r.comp, r.out, r.info, &S->whole_ws, &S->whole_cap,
+                                                              nullptr, stream);
+            if (rc) return undo(rc);
+            if (cudaMemcpyAsync(&S->h_status[slot], S->whole_ws + up256(sizeof(WsHead)) + offsetof(StreamState, status),
+                                4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+                return undo(kErrCuda);
+        }
         S->queue.pop_front();
         S->used += r.bytes;
         r.slot = slot;
         r.phase = 1;
         S->slot_owner[slot] = id;
-        if (aceapex_host::init_state(&S->d_state[slot], stream)) return kErrCuda;
         if (r.info.decoded_len == 0) {
             S->h_status[slot] = 0;
             r.phase = 2;
             r.done_step = S->step_no;
-        } else if (r.info.max_depth > 1) {
-            // deep stream: decoded whole, here
-            int rc = aceapex_host::server_enqueue_whole(r.comp, r.out, r.info, &S->whole_ws, &S->whole_cap,
-                                                        nullptr, stream);
-            if (rc) return rc;
+        } else if (r.whole) {
             r.phase = 2;
             r.done_step = S->step_no;
             r.next_tile = r.info.n_tiles;
-            // the whole-stream decode left its status in its workspace's state
-            if (cudaMemcpyAsync(&S->h_status[slot], S->whole_ws + up256(sizeof(WsHead)) + offsetof(StreamState, status), 4,
-                                cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-                return kErrCuda;
         }
     }
     // 2. slices: every admitted request with tiles left gets a share of the step's tile budget
     std::vector<int64_t> act;
     for (int k = 0; k < S->max_slots; k++) {
         const int64_t id = S->slot_owner[k];
-        if (id >= 0 && S->reqs[id].phase == 1) act.push_back(id);
+        if (id >= 0 && S->reqs[id].phase == 1 && !S->reqs[id].whole) act.push_back(id);
     }
     std::sort(act.begin(), act.end());
     StreamDesc *hd = S->h_descs + (size_t)ring * S->max_slots;
@@ -208,6 +228,7 @@ int aceapex_server_step(aceapex_server *S, void *stream_) {
             d.comp = (const uint8_t *)r.comp; d.out = (uint8_t *)r.out; d.comp_len = r.info.comp_len;
             d.N = r.info.decoded_len; d.n_blocks = r.info.n_blocks; d.n_seq = r.info.n_seq; d.n_match = r.info.n_match;
             d.tile_base = total; d.n_tiles = take; d.tile_off = r.next_tile; d.state = &S->d_state[r.slot];
+            d.litmap = r.litmap;
             d.block_log2 = r.info.block_log2; d.tile_log2 = r.info.tile_log2; d.min_match = r.info.min_match;
             d.max_depth = r.info.max_depth;
             d.flags = (r.next_tile + take == r.info.n_tiles) ? kDescLast : 0u;
@@ -267,6 +288,7 @@ int aceapex_server_release(aceapex_server *S, int64_t id, void *stream_) {
     if (r.phase != 2) return kErrArg;
     cudaFreeAsync(r.out, (cudaStream_t)stream_);
     r.out = nullptr;
+    r.litmap = nullptr;
     r.phase = 3;
     S->used -= r.bytes;
     S->slot_owner[r.slot] = -1;

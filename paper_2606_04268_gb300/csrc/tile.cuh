@@ -217,23 +217,4 @@ __device__ void chunk_literals(const TileSmem<NT, SPT> &sm, uint8_t *out) {
     }
 }
 
-// All threads: write the chunk's match bytes that fall inside the tile: out[d+k] = out[s + (k mod (d-s))].
-template <int NT, int SPT>
-__device__ void chunk_matches(const TileSmem<NT, SPT> &sm, uint8_t *out) {
-    const uint32_t n = sm.chunk_n;
-    const uint32_t lo = sm.start[0] > sm.tile_lo ? sm.start[0] : sm.tile_lo;
-    const uint32_t hi = sm.start[n] < sm.tile_hi ? sm.start[n] : sm.tile_hi;
-    uint8_t *ob = out + sm.b0;
-    for (uint32_t q = lo + threadIdx.x; q < hi; q += NT) {
-        const uint32_t i = seq_of(sm, n, q);
-        const uint32_t rel = q - sm.start[i];
-        if (rel >= sm.rlen[i]) {
-            const uint64_t k = rel - sm.rlen[i];
-            const uint64_t d = sm.b0 + sm.start[i] + sm.rlen[i], s = sm.soff[i], p = d - s;
-            const uint64_t src = s + (k < p ? k : k % p);
-            ob[q] = ld_out(out + src);
-        }
-    }
-}
-
 }  // namespace aceapex

@@ -10,7 +10,7 @@
 //   L2, since the previous level's bytes were written by other SMs), longer or self-overlapping matches are
 //   copied by the whole warp.
 #pragma once
-#include "flat3.cuh"
+#include "warp_tile.cuh"
 
 namespace aceapex {
 
@@ -327,7 +327,9 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
                         }
                     }
                     uint32_t dep = mx + 1;
-                    if (dep > cap) { report(&sst[0], kErrDepth, kOrderDepth); dep = cap; }
+                    // a match deeper than its block's max_depth field: the stream understates its depth
+                    if (L && dep > wb.bdepth[d >> sd.block_log2]) report_depth(&sst[0]);
+                    if (dep > cap) dep = cap;
                     st_release_u32(&wb.depth[m], dep);  // the bytes above are visible before the depth
                     mydep[sub] = dep;
                     dmax = dep > dmax ? dep : dmax;

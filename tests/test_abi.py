@@ -56,7 +56,9 @@ def test_peek_header_matches_oracle(lib, kw):
 
 @pytest.mark.parametrize("kind", ["markov", "text", "fastq", "random", "rle7"])
 @pytest.mark.parametrize("kw", [dict(), dict(flatten=1), dict(flatten=2, min_emit=6), dict(depth_cap=4, min_emit=6),
-                                dict(block_log2=10, tile_log2=4, flatten=2), dict(depth_cap=1, chain_limit=4)])
+                                dict(block_log2=10, tile_log2=4, flatten=2), dict(depth_cap=1, chain_limit=4),
+                                dict(flatten=2, min_emit=10, long_bits=16), dict(depth_cap=4, min_emit=10, long_bits=16),
+                                dict(flatten=1, long_bits=12, long_chain=2), dict(long_bits=20, long_chain=16)])
 def test_encoder_equals_oracle_encoder(lib, kind, kw):
     """The library's C++ encoder follows the same parse rules as the oracle's: identical streams."""
     x = synth.make(kind, 400_000, 8)
@@ -72,3 +74,9 @@ def test_encoder_rejects_bad_params(lib):
         ax.encode(b"abc", block_log2=30)
     with pytest.raises(ax.AceapexError):
         ax.encode(b"abc", chain_limit=64)
+    with pytest.raises(ax.AceapexError):
+        ax.encode(b"abc", long_bits=30)
+    with pytest.raises(ax.AceapexError):
+        ax.encode(b"abc", long_bits=16, long_chain=17)
+    with pytest.raises(oracle.OracleError):
+        oracle.encode(b"abc", long_bits=16, long_chain=0)

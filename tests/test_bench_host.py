@@ -21,11 +21,46 @@ def test_stream_stats_agree_with_the_oracle_parse():
 
 
 def test_kernel_bytes_are_the_stated_formulas():
+    """The method's bytes per launch (stream read once, output written once, match sources read once); the
+    wavefront path's own per-match records are reported apart."""
     st = dict(C=100, N=1000, match_bytes=600, lit_bytes=400, n_match=50)
     assert bench.kernel_bytes("k_flat", st) == 100 + 1000 + 600
-    assert bench.kernel_bytes("k_flow", st) == 2 * 600 + 28 * 50
-    assert bench.kernel_bytes("k_wave", st) == 2 * 600 + 24 * 50
+    assert bench.kernel_bytes("k_parse", st) == 100 + 1000
+    assert bench.kernel_bytes("k_flow", st) == 2 * 600
+    assert bench.kernel_bytes("k_wave", st) == 2 * 600
     assert bench.kernel_bytes("unknown", st) == 0.0
+    assert bench.metadata_bytes("k_flow", st) == 28 * 50 and bench.metadata_bytes("k_flat", st) == 0.0
+
+
+def test_batch_and_reference_configs_agree():
+    """Both arms of the bench print the same config for a workload; the batch's decoded bytes come from
+    the payload sizes alone."""
+    specs, which, N = bench.batch_plan_specs(0)
+    assert len(which) == bench.BATCH_STREAMS and len(specs) == bench.BATCH_UNIQUE
+    assert N == sum(specs[u][1] for u in which)
+    assert all(enc == bench.FLAT[k] for k, _, _, enc in specs)
+    assert bench.batch_config(1, N)["decoded_bytes"] == N
+    assert set(bench.EXTRAS) <= set(bench.WORKLOADS)
+
+
+def test_reference_sample_uses_the_oracle_only():
+    """The reference arm's sample is encoded by the oracle, with the workload's parameters, and is the
+    workload's own input (a block-aligned prefix): it decodes back to it."""
+    import argparse
+    import sys
+    args = argparse.Namespace(workload="small", gpus=1, size=0)
+    pool, cfg, sample = bench._reference_sample(args)
+    assert cfg == bench.single_config(args, 1)
+    (x, comp), = pool
+    assert np.array_equal(oracle.decode(comp), x)
+    assert np.array_equal(x, synth.make("markov", x.size, bench.stream_seed("markov", 0)))
+    # in a process of its own, the reference arm's sampling never imports the product package
+    import subprocess
+    code = ("import argparse, sys, bench; "
+            "bench._reference_sample(argparse.Namespace(workload='small', gpus=1, size=0)); "
+            "assert 'paper_2606_04268_gb300' not in sys.modules, 'product imported'")
+    r = subprocess.run([sys.executable, "-c", code], cwd=bench.ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
 
 
 def test_batch_mix_follows_its_distribution():

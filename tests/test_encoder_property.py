@@ -40,12 +40,14 @@ def _data(seed: int, n: int, alphabet: int, motif: int) -> np.ndarray:
 @given(seed=st.integers(0, 2**31 - 1), n=st.integers(0, 6000), alphabet=st.sampled_from([2, 4, 26, 256]),
        motif=st.integers(1, 50), block_log2=st.sampled_from([6, 8, 12]), tile=st.integers(2, 6),
        min_match=st.integers(1, 6), flatten=st.sampled_from([0, 1, 2]), depth_cap=st.sampled_from([0, 1, 2, 5]),
-       chain_limit=st.sampled_from([1, 4, 16]), use_first=st.sampled_from([0, 1]), min_emit=st.sampled_from([0, 6]))
+       chain_limit=st.sampled_from([1, 4, 16]), use_first=st.sampled_from([0, 1]), min_emit=st.sampled_from([0, 6]),
+       long_bits=st.sampled_from([0, 8, 12]), long_chain=st.sampled_from([1, 4, 16]))
 def test_encoders_agree_and_round_trip(seed, n, alphabet, motif, block_log2, tile, min_match, flatten, depth_cap,
-                                       chain_limit, use_first, min_emit):
+                                       chain_limit, use_first, min_emit, long_bits, long_chain):
     x = _data(seed, n, alphabet, motif)
     kw = dict(block_log2=block_log2, tile_log2=min(tile, block_log2), min_match=min_match, flatten=flatten,
-              depth_cap=depth_cap, chain_limit=chain_limit, use_first=use_first, min_emit=min_emit)
+              depth_cap=depth_cap, chain_limit=chain_limit, use_first=use_first, min_emit=min_emit,
+              long_bits=long_bits, long_chain=long_chain)
     a = oracle.encode(x, **kw)
     b = ax.encode(x, **kw)
     assert np.array_equal(a, b)

@@ -9,6 +9,7 @@ import oracle
 import paper_2606_04268_gb300 as ax
 import synth
 from gpu_util import first_diff, gpu_decode, to_dev
+from stream_edit import block_depths, lower_depths, set_depths
 
 pytestmark = pytest.mark.gpu
 
@@ -24,13 +25,12 @@ def _lib():
 
 
 def set_path(path: str):
-    """auto: one-pass kernel (staged warp-per-tile variant) for depth <= 1, warp dataflow otherwise;
-    warp: the same with the unstaged warp-per-tile one-pass variant; w5: with the 128-sequences-per-step
-    staged variant; wave: level queues for every stream;
-    flow: per-match dataflow for every stream; wflow: warp dataflow for every stream."""
+    """auto: the one-pass kernel for the streams it takes (depth <= 1, tiles <= 4 KiB), warp dataflow for the
+    others; w2 / w8: the same with 2 / 8 warps per CTA of the one-pass kernel; wave: level queues for every
+    stream; flow: per-match dataflow for every stream; wflow: warp dataflow for every stream."""
     ax.set_force_wavefront(path in ("wave", "flow", "wflow"))
     ax.set_wave_scheduler({"flow": 0, "wave": 1}.get(path, 2))
-    ax.set_one_pass_kernel({"warp": 0, "w5": 4}.get(path, 3))
+    ax.set_launch_config({"w2": 2, "w8": 8}.get(path, 4), 0)
 
 
 def check(x: np.ndarray, comp: np.ndarray, path: str = "auto", offset: int = 0):
@@ -69,7 +69,7 @@ def test_kinds_modes_shapes(kind, mode, shape):
     n = 700_001 if shape[0] >= 16 else 90_001
     x = synth.make(kind, n, hash((kind, mode, shape)) & 0xFFFF)
     comp = oracle.encode(x, block_log2=shape[0], tile_log2=shape[1], **MODES[mode])
-    for path in ("auto", "warp", "w5", "wave", "flow", "wflow"):
+    for path in ("auto", "w2", "w8", "wave", "flow", "wflow"):
         check(x, comp, path)
 
 
@@ -81,7 +81,7 @@ def test_sizes_and_ragged_tails(n, kind):
     for kw in (dict(), dict(flatten=2)):
         comp = oracle.encode(x, **kw)
         check(x, comp, "auto")
-        check(x, comp, "w5")
+        check(x, comp, "w8")
 
 
 def test_empty_stream():
@@ -104,7 +104,7 @@ def test_self_overlapping_periods(period):
         d = np.cumsum(r + L) - L
         if period > 1:
             assert np.any((L > 0) & (d - s < L)), "expected self-overlapping matches"
-        for path in ("auto", "warp", "w5", "wave", "flow", "wflow"):
+        for path in ("auto", "w2", "w8", "wave", "flow", "wflow"):
             check(x, comp, path)
 
 
@@ -115,7 +115,7 @@ def test_unaligned_output(offset):
     check(x, comp, "auto", offset=offset)
     check(x, comp, "wave", offset=offset)
     check(x, comp, "wflow", offset=offset)
-    check(x, comp, "w5", offset=offset)
+    check(x, comp, "w2", offset=offset)
 
 
 @pytest.mark.parametrize("path", ["auto", "wave", "flow", "wflow"])
@@ -167,7 +167,7 @@ def test_malformed_stream_rejected_like_oracle(name):
     c = cases[name]
     rc_o, _ = oracle.decode_rc(c, out_len=x.size)
     assert rc_o != 0
-    for path in ("auto", "warp", "w5", "wave", "flow", "wflow"):
+    for path in ("auto", "w2", "w8", "wave", "flow", "wflow"):
         set_path(path)
         try:
             rc, _ = gpu_decode(c, x.size)
@@ -258,12 +258,13 @@ def test_bounded_wait_times_out_and_context_survives():
     check(x, comp, "auto")
 
 
-@pytest.mark.parametrize("cfg", [(128, 4), (128, 8), (256, 2), (256, 8), (512, 2), (512, 4)])
+@pytest.mark.parametrize("cfg", [(2, 0), (2, 3), (4, 2), (4, 4), (8, 0), (8, 1)])
 def test_launch_shapes(cfg):
     x = synth.make("fastq", 1_500_000, 5)
     comp = oracle.encode(x, flatten=2, min_emit=6)
-    ax.set_launch_config(cfg[0], 2, cfg[1])
+    ax.set_launch_config(*cfg)
     try:
+        assert ax.get_launch_config() == cfg
         check(x, comp, "auto")
     finally:
-        ax.set_launch_config(256, 0, 4)
+        ax.set_launch_config(4, 0)

@@ -14,9 +14,9 @@ import paper_2606_04268_gb300 as ax
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 GiB = 1 << 30
-FULL = [("text", GiB, bench.stream_seed("text", 0), dict(min_emit=6)),
-        ("fastq", GiB, bench.stream_seed("fastq", 0), dict(flatten=2, min_emit=6)),
-        ("fastq", GiB, bench.stream_seed("fastq", 0), dict(depth_cap=4, min_emit=6))]
+# the bench's single-stream workloads, with the bench's encoder parameters
+FULL = [(bench.WORKLOADS[w][0], bench.WORKLOADS[w][1], bench.stream_seed(bench.WORKLOADS[w][0], 0), bench.WORKLOADS[w][2])
+        for w in ("text", "fastq-flat", "fastq-cap4")]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -62,13 +62,11 @@ def test_full_size_workload_decodes_exactly(spec):
 def test_full_size_batch_graph_replay():
     """The batched configuration at full size: 4096 streams (256 distinct payloads from the batched mix,
     each placed 16 times), ~8 GiB of output, one plan replayed as a CUDA graph twice."""
-    mix = __import__("synth").batch_mix(256, seed=4000)
-    pool = bench.encode_pool([(k, n, sd, dict(flatten=2, min_emit=6) if k != "random" else dict(flatten=2))
-                              for k, n, sd in mix])
-    which = [i % 256 for i in range(4096)]
+    specs, which, N = bench.batch_plan_specs(0)
+    pool = bench.encode_pool(specs)
     c_off = np.cumsum([0] + [pool[u][1].size for u in which])
     o_off = np.cumsum([0] + [pool[u][0].size for u in which])
-    assert o_off[-1] > 6 * GiB
+    assert o_off[-1] == N > 6 * GiB
     d_comp = torch.empty(int(c_off[-1]), dtype=torch.uint8, device="cuda")
     uniq = [torch.from_numpy(c).cuda() for _, c in pool]
     for i, u in enumerate(which):

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import synth
+from stream_edit import block_offsets, lower_depths, set_depths
 
 KINDS = ["markov", "text", "fastq", "random", "rle7"]
 MODES = [dict(flatten=0), dict(flatten=1), dict(flatten=2), dict(depth_cap=4), dict(depth_cap=1),
@@ -145,25 +146,7 @@ def test_malformed_streams_rejected():
 
 
 # ---------------------------------------------------------------------------------------------- depth fields
-def _block_offsets(comp):
-    nb = int.from_bytes(bytes(comp[24:32]), "little")
-    return [int.from_bytes(bytes(comp[64 + 8 * b:72 + 8 * b]), "little") for b in range(nb)]
-
-
-def _set_depths(comp, block_depths, stream_depth):
-    """Overwrite the blocks' and the stream's max_depth fields (format §1.1, §2.1)."""
-    c = comp.copy()
-    for off, dep in zip(_block_offsets(c), block_depths):
-        c[off + 24:off + 28] = np.frombuffer(int(dep).to_bytes(4, "little"), np.uint8)
-    c[48:52] = np.frombuffer(int(stream_depth).to_bytes(4, "little"), np.uint8)
-    return c
-
-
-def lower_depths(comp, to=1):
-    """Every depth field clipped to `to`: a stream whose headers understate its matches' depths."""
-    offs = _block_offsets(comp)
-    deps = [min(int.from_bytes(bytes(comp[o + 24:o + 28]), "little"), to) for o in offs]
-    return _set_depths(comp, deps, max(deps, default=0))
+_set_depths, lower_depths = set_depths, lower_depths
 
 
 # two blocks of 16 bytes; block 0: (d 4, s 0, L 4) depth 1 and (d 9, s 0, L 4) depth 1; block 1: (d 20, s 4,
@@ -209,7 +192,7 @@ def test_depth_lie_reported_after_other_errors():
     assert oracle.peek(comp).max_depth >= 2
     lie = lower_depths(comp, 1)
     assert oracle.decode_rc(lie)[0] == -8
-    offs = _block_offsets(lie)
+    offs = block_offsets(lie)
     bad = _mut(lie, offs[-1] + 32 + 20 + 16, 4, 1)             # last block, sync entry 1 out_pos
     assert oracle.decode_rc(bad)[0] == -2
 

@@ -54,11 +54,30 @@ def test_noalloc_rejects_what_does_not_fit():
     with pytest.raises(ax.AceapexError) as e:
         ax.decode_noalloc(_dev(deep), torch.empty(x.size, dtype=torch.uint8, device="cuda"), info, st)
     assert e.value.code == ax.ERR_NOMEM
-    # more tiles than the fixed flag array holds (tiles of 4 bytes)
-    y = synth.make("random", 1_200_000, 6)
+    # more tile flags and literal bits than the fixed 16 MiB array holds (16 MiB of output in 4-byte tiles)
+    y = synth.make("rle7", 16 << 20, 6)
     many = oracle.encode(y, flatten=2, block_log2=12, tile_log2=2)
     info2 = ax.peek_header(many[:64])
-    assert info2.n_tiles > 261_888
+    assert 4 * info2.n_tiles + info2.decoded_len // 8 > 16 << 20
     with pytest.raises(ax.AceapexError) as e:
         ax.decode_noalloc(_dev(many), torch.empty(y.size, dtype=torch.uint8, device="cuda"), info2, st)
     assert e.value.code == ax.ERR_NOMEM
+
+
+def test_noalloc_reports_depth_lie_like_regular_decode():
+    """A stream whose depth fields understate its matches' depths ends in ERR_DEPTH on both entry points."""
+    from stream_edit import lower_depths
+    ax.build()
+    x = synth.make("text", 400_000, 43)
+    lie = lower_depths(oracle.encode(x, block_log2=16, tile_log2=12, depth_cap=2), 1)
+    info = ax.peek_header(lie[:64])
+    assert info.max_depth == 1
+    d_comp = _dev(lie)
+    out = torch.empty(x.size, dtype=torch.uint8, device="cuda")
+    rc = ax.decode_status(d_comp, out)
+    assert rc == ax.ERR_DEPTH
+    for _ in range(2):
+        st = torch.full((1,), 77, dtype=torch.int32, device="cuda")
+        ax.decode_noalloc(d_comp, out, info, st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == rc
