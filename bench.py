@@ -324,8 +324,8 @@ def _reference_sample(args):
     oracle.build()
     world = args.gpus
     if args.workload == "batch":
-        specs, which, N = batch_plan_specs(0)
-        cfg = batch_config(world, N)
+        specs, which, N = batch_plan_specs(0, args.batch_streams)
+        cfg = batch_config(world, N, args.batch_streams)
     elif args.workload == "serve":
         specs = [(k, n, sd, FLAT[k]) for k, n, sd in synth.serve_mix(SERVE_POOL, seed=5000)]
         cfg = serve_config(world)
@@ -552,17 +552,18 @@ def _cpu_sample(comps, xs, seconds):
     return done / t_total / 1e9, n_streams, done, t_total
 
 
-def batch_plan_specs(rank: int):
-    """The batch workload: payload specs (kind, size, seed, encoder params), which payload each of the 4096
-    streams carries, and the decoded bytes of all streams."""
+def batch_plan_specs(rank: int, n_streams: int = BATCH_STREAMS):
+    """The batch workload: payload specs (kind, size, seed, encoder params), which payload each of the
+    n_streams streams carries (4096 in the workload; fewer for a small profiling case), and the decoded
+    bytes of all streams."""
     mix = synth.batch_mix(BATCH_UNIQUE, seed=4000 + rank)
     specs = [(k, n, sd, FLAT[k]) for k, n, sd in mix]
-    which = [i % BATCH_UNIQUE for i in range(BATCH_STREAMS)]  # stream i carries payload i mod 256
+    which = [i % BATCH_UNIQUE for i in range(n_streams)]  # stream i carries payload i mod 256
     return specs, which, int(sum(specs[u][1] for u in which))
 
 
-def batch_config(world: int, N: int):
-    return {"workload": WORKLOADS["batch"][3], "streams": BATCH_STREAMS, "distinct_payloads": BATCH_UNIQUE,
+def batch_config(world: int, N: int, n_streams: int = BATCH_STREAMS):
+    return {"workload": WORKLOADS["batch"][3], "streams": n_streams, "distinct_payloads": BATCH_UNIQUE,
             "decoded_bytes": N, "parallelism": f"replicas x{world}",
             "l2": "inputs and outputs larger than L2 (no flush needed)"}
 
@@ -588,7 +589,7 @@ def run_batch(args):
     ext_pool, ext_job = _start_extras() if extras else (None, None)
     torch.cuda.set_device(local)
     ax.build()
-    specs, which, N = batch_plan_specs(rank)
+    specs, which, N = batch_plan_specs(rank, args.batch_streams)
     t0 = time.time()
     pool = encode_pool(specs)
     enc_s = time.time() - t0
@@ -684,7 +685,7 @@ def run_batch(args):
     st = {"C": C, "N": N, "match_bytes": N - n_lit, "lit_bytes": n_lit, "n_match": n_match}
     roof, kms, _, launches = _roofline(prof, st, args.steps, hbm_peak, peak_kind, "batch")
     line = _base_line(args, value, ms, WORKLOADS["batch"][3],
-                      {k: v for k, v in batch_config(world, N).items() if k != "workload"})
+                      {k: v for k, v in batch_config(world, N, n_streams).items() if k != "workload"})
     line["details"] = {"comp_bytes": C, "ratio": round(C / N, 4), "n_match": n_match,
                        "mean_match": round((N - n_lit) / max(n_match, 1), 2),
                        "autotuned": {"warps_per_cta": cfg[0], "ctas_per_sm": cfg[1]},
@@ -892,6 +893,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch", choices=list(WORKLOADS))
+    ap.add_argument("--batch-streams", type=int, default=BATCH_STREAMS,
+                    help="streams of the batch workload (4096; fewer for a small profiling case)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="batch workload: skip the single-stream configurations measured beside it")
     ap.add_argument("--size", type=int, default=0, help="override the workload size (bytes)")

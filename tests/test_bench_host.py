@@ -48,7 +48,7 @@ def test_reference_sample_uses_the_oracle_only():
     workload's own input (a block-aligned prefix): it decodes back to it."""
     import argparse
     import sys
-    args = argparse.Namespace(workload="small", gpus=1, size=0)
+    args = argparse.Namespace(workload="small", gpus=1, size=0, batch_streams=4096)
     pool, cfg, sample = bench._reference_sample(args)
     assert cfg == bench.single_config(args, 1)
     (x, comp), = pool
@@ -57,7 +57,7 @@ def test_reference_sample_uses_the_oracle_only():
     # in a process of its own, the reference arm's sampling never imports the product package
     import subprocess
     code = ("import argparse, sys, bench; "
-            "bench._reference_sample(argparse.Namespace(workload='small', gpus=1, size=0)); "
+            "bench._reference_sample(argparse.Namespace(workload='small', gpus=1, size=0, batch_streams=4096)); "
             "assert 'paper_2606_04268_gb300' not in sys.modules, 'product imported'")
     r = subprocess.run([sys.executable, "-c", code], cwd=bench.ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
