@@ -517,6 +517,7 @@ def run_ours(args):
         v, reps, secs = cpu_oracle_baseline(comp, r["decoded_bytes"], args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"the workload's stream decoded {reps} times ({secs:.1f} s)"}
+        line["cpu_baseline_parallel"] = _cpu_par_line([comp], [x], args.cpu_seconds, "the workload's stream")
         if args.cpu_all_cores:
             rr = cpu_oracle_all_cores(comp, r["decoded_bytes"])
             if rr:
@@ -550,6 +551,33 @@ def _cpu_sample(comps, xs, seconds):
         if t_total >= seconds:
             break
     return done / t_total / 1e9, n_streams, done, t_total
+
+
+def _cpu_par_sample(comps, xs, seconds):
+    """The block-parallel CPU decoder (threads over blocks in order, paper §3.1) on all host cores, whole
+    streams of a workload in order, for about `seconds`; returns (GB/s, threads, streams, bytes, seconds)."""
+    import platform
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    done, t_total, n_streams = 0, 0.0, 0
+    while t_total < seconds:
+        for comp, x in zip(comps, xs):
+            t0 = time.perf_counter()
+            rc, _ = oracle.cpupar_decode_rc(comp, x.size, threads=threads)
+            t_total += time.perf_counter() - t0
+            assert rc == 0
+            done += x.size
+            n_streams += 1
+            if t_total >= seconds:
+                break
+    return done / t_total / 1e9, threads, n_streams, done, t_total, platform.processor() or platform.machine()
+
+
+def _cpu_par_line(comps, xs, seconds, what):
+    v, th, ns, nb, secs, cpu = _cpu_par_sample(comps, xs, seconds)
+    return {"value": round(v, 4), "unit": "GB/s", "cores": th, "kind": "block-parallel CPU decoder",
+            "cpu": cpu, "sample": f"{what}: {ns} stream decodes ({nb} bytes, {secs:.1f} s)"}
 
 
 def batch_plan_specs(rank: int, n_streams: int = BATCH_STREAMS):
@@ -701,6 +729,7 @@ def run_batch(args):
         v, ns, nb, secs = _cpu_sample(cs, xs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"the first {ns} distinct streams of the batch ({nb} bytes, {secs:.1f} s)"}
+        line["cpu_baseline_parallel"] = _cpu_par_line(cs, xs, args.cpu_seconds, "the batch's distinct streams")
     del d_comp, d_out, comps, outs, h_comp, h_out
     torch.cuda.empty_cache()
     if extras:

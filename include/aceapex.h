@@ -196,6 +196,21 @@ int aceapex_profile_read(int max_kernels, const char **names, double *total_ms, 
 /* Statistics of the last aceapex_decode on this context (level histogram only when the wavefront ran). */
 int aceapex_get_stats(aceapex_stats *stats);
 
+/* Pre-scan choice between a CPU and a GPU decode (paper §8, data characteristics and GPU suitability: the
+ * size and the depth of a stream, read from its header, decide which processor decodes it faster).  The
+ * model is in decoded GB/s and microseconds; fields left at 0 take the defaults measured on GB300
+ * (one-pass 260 GB/s; wavefront 200 GB/s plus 16.5 us per dependency level; 30 us fixed per decode).
+ * cpu_gbps (required, > 0) is the caller's own CPU decode rate, measured on its host; link_gbps > 0 adds
+ * the copy of the stream and the output between host and device to the GPU time (0: device-resident). */
+typedef struct {
+    double cpu_gbps, gpu_one_pass_gbps, gpu_wave_gbps, gpu_level_us, gpu_fixed_us, link_gbps;
+} aceapex_device_model;
+
+/* Returns 1 when the GPU decode is estimated faster, 0 when the CPU decode is, ACEAPEX_ERR_ARG for a null
+ * pointer or cpu_gbps <= 0.  *cpu_s and *gpu_s (may be null) receive the two estimates in seconds.  Streams
+ * the one-pass kernel takes (see aceapex_set_force_wavefront) are estimated at the one-pass rate. */
+int aceapex_choose_device(const aceapex_info *info, const aceapex_device_model *model, double *cpu_s, double *gpu_s);
+
 /* Human-readable name of a status code. */
 const char *aceapex_strerror(int code);
 

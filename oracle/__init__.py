@@ -2,9 +2,10 @@
 
 Plain sequential C (``oracle.c``) restating the paper's method: the encoder (§3.1 absolute offsets,
 §3.3 chain flattening, §7.4 depth cap), the decoder that defines the decoded bytes (§3.2), a textbook
-relative-distance LZ77 decoder (§2), per-match depth (§7.1) and the stream invariants.  Only the test
-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg use it; the product package never
-imports it and shares no code with it.
+relative-distance LZ77 decoder (§2), per-match depth (§7.1) and the stream invariants.  Beside it,
+``cpupar.c``: the paper's block-parallel multi-threaded CPU decoder (§3.1), a CPU baseline, not the
+oracle.  Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg use them; the
+product package never imports them and shares no code with them.
 """
 from __future__ import annotations
 
@@ -43,12 +44,44 @@ class Info(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (plain gcc -O2)."""
+    """Compile oracle.c into liboracle.so next to it (plain gcc -O2), and the block-parallel CPU decoder."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
+    build_cpupar(force)
     return _LIB_PATH
+
+
+_PAR_SRC = os.path.join(_HERE, "cpupar.c")
+_PAR_PATH = os.path.join(_HERE, "libcpupar.so")
+_par = None
+
+
+def build_cpupar(force: bool = False) -> str:
+    """Compile the block-parallel CPU decoder (cpupar.c, a CPU baseline, not the oracle) next to it."""
+    if force or not os.path.exists(_PAR_PATH) or os.path.getmtime(_PAR_PATH) < os.path.getmtime(_PAR_SRC):
+        tmp = _PAR_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, _PAR_SRC])
+        os.replace(tmp, _PAR_PATH)
+    return _PAR_PATH
+
+
+def cpupar_decode_rc(comp, out_len: int | None = None, threads: int | None = None):
+    """Block-parallel CPU decode (§3.1: threads over blocks in order): (status, bytes or None)."""
+    global _par
+    with _lock:
+        if _par is None:
+            lib = ctypes.CDLL(build_cpupar())
+            lib.cpupar_decode.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]
+            lib.cpupar_decode.restype = ctypes.c_int
+            _par = lib
+    c = _u8(comp)
+    if out_len is None:
+        out_len = int.from_bytes(bytes(c[16:24]), "little")
+    out = np.zeros(max(out_len, 1), dtype=np.uint8)
+    rc = _par.cpupar_decode(c.ctypes.data, c.size, out.ctypes.data, out_len, int(threads or os.cpu_count() or 1))
+    return rc, (out[:out_len] if rc == 0 else None)
 
 
 def _load():

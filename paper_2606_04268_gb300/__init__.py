@@ -101,6 +101,11 @@ class Stats(ctypes.Structure):
                [("level_hist", ctypes.c_uint64 * HIST_MAX), ("phase_cycles", ctypes.c_uint64 * 8)]
 
 
+class DeviceModel(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("cpu_gbps", "gpu_one_pass_gbps", "gpu_wave_gbps", "gpu_level_us", "gpu_fixed_us", "link_gbps")]
+
+
 class EncParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("block_log2", "tile_log2", "min_match", "hash_bits", "chain_limit", "flatten", "depth_cap",
@@ -116,7 +121,7 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
            "aceapex_server_release", "aceapex_server_destroy",
-           "aceapex_encode", "aceapex_free"]
+           "aceapex_encode", "aceapex_free", "aceapex_choose_device"]
 
 _lib = None
 _lock = threading.Lock()
@@ -161,6 +166,8 @@ def lib():
             L.aceapex_server_poll.argtypes = [p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(p)]
             L.aceapex_server_release.argtypes = [p, ctypes.c_int64, p]
             L.aceapex_server_destroy.argtypes = [p]
+            L.aceapex_choose_device.argtypes = [ctypes.POINTER(Info), ctypes.POINTER(DeviceModel),
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.aceapex_encode.argtypes = [p, sz, ctypes.POINTER(EncParams), ctypes.POINTER(p)]
             L.aceapex_encode.restype = ctypes.c_int64
             L.aceapex_free.argtypes = [p]
@@ -386,6 +393,19 @@ def get_launch_config():
     w, c = ctypes.c_int(), ctypes.c_int()
     _check(lib().aceapex_get_launch_config(ctypes.byref(w), ctypes.byref(c)), "get_launch_config")
     return w.value, c.value
+
+
+def choose_device(info: Info, cpu_gbps: float, link_gbps: float = 0.0, **model) -> tuple:
+    """Pre-scan choice between a CPU and a GPU decode from the stream's header (aceapex_choose_device):
+    returns ("gpu" or "cpu", estimated CPU seconds, estimated GPU seconds).  model: gpu_one_pass_gbps,
+    gpu_wave_gbps, gpu_level_us, gpu_fixed_us (0 = the library's GB300 defaults)."""
+    m = DeviceModel(cpu_gbps, model.get("gpu_one_pass_gbps", 0.0), model.get("gpu_wave_gbps", 0.0),
+                    model.get("gpu_level_us", 0.0), model.get("gpu_fixed_us", 0.0), link_gbps)
+    tc, tg = ctypes.c_double(), ctypes.c_double()
+    rc = lib().aceapex_choose_device(ctypes.byref(info), ctypes.byref(m), ctypes.byref(tc), ctypes.byref(tg))
+    if rc < 0:
+        raise AceapexError(rc, "aceapex_choose_device")
+    return ("gpu" if rc == 1 else "cpu"), tc.value, tg.value
 
 
 def set_wave_scheduler(kind: int) -> None:

@@ -760,6 +760,26 @@ int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t
     return *h_status;
 }
 
+int aceapex_choose_device(const aceapex_info *info, const aceapex_device_model *model, double *cpu_s, double *gpu_s) {
+    if (!info || !model || !(model->cpu_gbps > 0)) return kErrArg;
+    const double one = model->gpu_one_pass_gbps > 0 ? model->gpu_one_pass_gbps : 260.0;
+    const double wave = model->gpu_wave_gbps > 0 ? model->gpu_wave_gbps : 200.0;
+    const double level_s = 1e-6 * (model->gpu_level_us > 0 ? model->gpu_level_us : 16.5);
+    const double fixed_s = 1e-6 * (model->gpu_fixed_us > 0 ? model->gpu_fixed_us : 30.0);
+    const double N = (double)info->decoded_len, C = (double)info->comp_len;
+    const double tc = N / (model->cpu_gbps * 1e9);
+    bool one_pass;
+    {
+        std::lock_guard<std::mutex> g(ctx().mu);
+        one_pass = !use_wave(*info);
+    }
+    double tg = fixed_s + (one_pass ? N / (one * 1e9) : N / (wave * 1e9) + level_s * info->max_depth);
+    if (model->link_gbps > 0) tg += (C + N) / (model->link_gbps * 1e9);
+    if (cpu_s) *cpu_s = tc;
+    if (gpu_s) *gpu_s = tg;
+    return tg < tc ? 1 : 0;
+}
+
 const char *aceapex_strerror(int code) {
     switch (code) {
         case kOK: return "ok";
