@@ -83,7 +83,10 @@ def stream_stats(comp: np.ndarray):
 # DRAM bytes (read + write) per decoded byte of the dominant kernel, from one ncu capture of a 256 MiB case
 # of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / decoded bytes),
 # scaled to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
-MEASURED_TRAFFIC_PER_BYTE = {}
+MEASURED_TRAFFIC_PER_BYTE = {
+    ("fastq-flat", "k_flat"): 2.6914,  # 440,329,728 + 282,149,120 bytes, 256 MiB flattened FASTQ, one k_flat launch
+    ("text", "k_flow"): 7.1587,        # 1,504,913,408 + 416,750,592 bytes, 256 MiB deep text, one k_flow launch
+}
 
 
 def kernel_bytes(name: str, st: dict) -> float:
