@@ -222,7 +222,8 @@ const char *aceapex_strerror(int code);
  * allocator), then enqueues ONE one-pass launch that advances every admitted request by a slice of its tiles
  * (each request gets an equal share of tiles_per_step); requests admitted while others are running join the
  * next launch.  A stream the one-pass kernel does not take (deeper than 1, tiles over 4 KiB) is decoded
- * whole in the step that admits it.  poll returns 1 once a
+ * whole by the wavefront path on a stream the server owns, enqueued in the step that admits it, so the
+ * other requests' launches do not wait for it.  poll returns 1 once a
  * request's last launch has completed (with its status and output pointer), 0 while pending; release frees
  * its output and budget (stream-ordered on `stream`).  step returns the number of queued + running
  * requests.  One host thread drives a server; the budget counts stream + output bytes (plus, for a request

@@ -6,8 +6,9 @@
 // every admitted request by a slice of its tiles: a request's slices run in order (consecutive steps on one
 // stream), each starting after the tiles that earlier steps decoded, so requests that arrive while others
 // are on the GPU join the next launch and share it.  A request is done when the launch holding its last
-// slice has completed (CUDA event).  Streams whose matches are deeper than 1 are decoded whole (wavefront
-// path) in the step that admits them.
+// slice has completed (CUDA event).  Streams whose matches are deeper than 1 are decoded whole by the
+// wavefront path on the server's own side stream, enqueued in the step that admits them: the sliced
+// launches of the other requests do not wait behind them.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -50,6 +51,7 @@ struct Req {
 };
 
 constexpr int kMaxStepsInFlight = 4;
+constexpr unsigned kEvFlags = cudaEventDisableTiming;
 
 }  // namespace
 
@@ -69,15 +71,20 @@ struct aceapex_server {
     int32_t *h_status = nullptr;      // pinned, one per slot
     cudaEvent_t ev[kMaxStepsInFlight]{};
     long step_no = 0;
-    uint8_t *whole_ws = nullptr;      // wavefront workspace for deep streams
+    uint8_t *whole_ws = nullptr;      // wavefront workspace for deep streams (used in order on `side`)
     size_t whole_cap = 0;
+    cudaStream_t side = nullptr;      // whole decodes of deep streams
+    cudaEvent_t admitted = nullptr;   // side waits for the admission work (allocation, state) on the step stream
+    std::vector<cudaEvent_t> slot_ev; // per slot: completion of a whole decode (created on first use)
 };
 
 namespace {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-bool event_done(aceapex_server *S, long step) {
+bool event_done(aceapex_server *S, const Req &r) {
+    if (r.whole && r.info.decoded_len > 0) return cudaEventQuery(S->slot_ev[r.slot]) == cudaSuccess;
+    const long step = r.done_step;
     if (step < 0) return false;
     // the ring entry of step k is waited for at the start of step k + kMaxStepsInFlight
     if (step + kMaxStepsInFlight < S->step_no) return true;
@@ -105,9 +112,15 @@ int aceapex_server_create(size_t hbm_budget, int max_slots, uint64_t tiles_per_s
               cudaMallocHost((void **)&S->h_status, sizeof(int32_t) * max_slots) == cudaSuccess &&
               cudaMemset(S->d_ws, 0, S->ws_stride * kMaxStepsInFlight) == cudaSuccess;
     for (int k = 0; ok && k < kMaxStepsInFlight; k++)
-        ok = cudaEventCreateWithFlags(&S->ev[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = cudaEventCreateWithFlags(&S->ev[k], kEvFlags) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&S->admitted, kEvFlags) == cudaSuccess;
+    if (ok) S->slot_ev.assign(max_slots, nullptr);
     if (!ok) {
         cudaGetLastError();
+        for (int k = 0; k < kMaxStepsInFlight; k++) if (S->ev[k]) cudaEventDestroy(S->ev[k]);
+        if (S->admitted) cudaEventDestroy(S->admitted);
+        if (S->side) cudaStreamDestroy(S->side);
         cudaFree(S->d_state); cudaFree(S->d_ws); cudaFreeHost(S->h_descs); cudaFreeHost(S->h_status);
         delete S;
         return kErrNomem;
@@ -121,6 +134,9 @@ int aceapex_server_destroy(aceapex_server *S) {
     cudaDeviceSynchronize();
     for (auto &r : S->reqs) if (r.out && r.phase != 3) cudaFree(r.out);
     for (int k = 0; k < kMaxStepsInFlight; k++) if (S->ev[k]) cudaEventDestroy(S->ev[k]);
+    for (cudaEvent_t e : S->slot_ev) if (e) cudaEventDestroy(e);
+    if (S->admitted) cudaEventDestroy(S->admitted);
+    if (S->side) cudaStreamDestroy(S->side);
     cudaFree(S->d_state); cudaFree(S->d_ws); cudaFree(S->whole_ws);
     cudaFreeHost(S->h_descs); cudaFreeHost(S->h_status);
     delete S;
@@ -168,6 +184,7 @@ int aceapex_server_step(aceapex_server *S, void *stream_) {
         }
         r.litmap = r.whole ? nullptr : (uint32_t *)((uint8_t *)r.out + align16(r.info.decoded_len));
         auto undo = [&](int rc) {
+            if (r.whole) cudaStreamSynchronize(S->side);  // nothing of a failed whole decode may still run
             cudaFreeAsync(r.out, stream);
             cudaGetLastError();
             r.out = nullptr;
@@ -176,13 +193,22 @@ int aceapex_server_step(aceapex_server *S, void *stream_) {
         };
         if (aceapex_host::init_state(&S->d_state[slot], stream)) return undo(kErrCuda);
         if (r.info.decoded_len > 0 && r.whole) {
-            // deep stream (or one the one-pass kernel does not take): decoded whole, here; its status is
-            // left in its workspace's state
+            // deep stream (or one the one-pass kernel does not take): decoded whole on the side stream, after
+            // the admission work above; its status is left in the shared workspace's state and copied out
+            // before the next whole decode can reuse the workspace (same stream)
+            if (!S->slot_ev[slot] && cudaEventCreateWithFlags(&S->slot_ev[slot], kEvFlags) != cudaSuccess) {
+                S->slot_ev[slot] = nullptr;
+                return undo(kErrCuda);
+            }
+            if (cudaEventRecord(S->admitted, stream) != cudaSuccess ||
+                cudaStreamWaitEvent(S->side, S->admitted, 0) != cudaSuccess)
+                return undo(kErrCuda);
             const int rc = aceapex_host::server_enqueue_whole(r.comp, r.out, r.info, &S->whole_ws, &S->whole_cap,
-                                                              nullptr, stream);
+                                                              nullptr, S->side);
             if (rc) return undo(rc);
             if (cudaMemcpyAsync(&S->h_status[slot], S->whole_ws + up256(sizeof(WsHead)) + offsetof(StreamState, status),
-                                4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+                                4, cudaMemcpyDeviceToHost, S->side) != cudaSuccess ||
+                cudaEventRecord(S->slot_ev[slot], S->side) != cudaSuccess)
                 return undo(kErrCuda);
         }
         S->queue.pop_front();
@@ -274,7 +300,7 @@ int aceapex_server_poll(aceapex_server *S, int64_t id, int32_t *status, void **o
     std::lock_guard<std::mutex> g(S->mu);
     if (id < 0 || id >= (int64_t)S->reqs.size()) return kErrArg;
     Req &r = S->reqs[id];
-    if (r.phase != 2 || !event_done(S, r.done_step)) return 0;
+    if (r.phase != 2 || !event_done(S, r)) return 0;
     if (status) *status = S->h_status[r.slot];
     if (out) *out = r.out;
     return 1;
@@ -286,6 +312,9 @@ int aceapex_server_release(aceapex_server *S, int64_t id, void *stream_) {
     if (id < 0 || id >= (int64_t)S->reqs.size()) return kErrArg;
     Req &r = S->reqs[id];
     if (r.phase != 2) return kErrArg;
+    // a whole decode runs on the side stream: the free waits for it (stream-ordered)
+    if (r.whole && r.info.decoded_len > 0 && cudaStreamWaitEvent((cudaStream_t)stream_, S->slot_ev[r.slot], 0) != cudaSuccess)
+        return kErrCuda;
     cudaFreeAsync(r.out, (cudaStream_t)stream_);
     r.out = nullptr;
     r.litmap = nullptr;
