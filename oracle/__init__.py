@@ -108,6 +108,8 @@ def _load():
             lib.oracle_depths.argtypes = [p, u64, p, u64]
             lib.oracle_depths.restype = i64
             lib.oracle_check.argtypes = [p, u64]
+            lib.oracle_transcode_flat.restype = ctypes.c_int64
+            lib.oracle_transcode_flat.argtypes = [p, u64, pp]
             lib.oracle_check.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -231,3 +233,20 @@ def check(comp) -> int:
     """0 when every invariant holds; see oracle_check in oracle.c for the codes."""
     c = _u8(comp)
     return _load().oracle_check(c.ctypes.data, c.size)
+
+
+def transcode_flat_rc(comp):
+    """Global chain flattening of an existing stream (oracle_transcode_flat): (0, stream) or (status, None)."""
+    c = _u8(comp)
+    ptr = ctypes.c_void_p()
+    n = _load().oracle_transcode_flat(c.ctypes.data, c.size, ctypes.byref(ptr))
+    if n < 0:
+        return int(n), None
+    return 0, _take(ptr, n)
+
+
+def transcode_flat(comp) -> np.ndarray:
+    rc, out = transcode_flat_rc(comp)
+    if rc:
+        raise OracleError(rc, "oracle_transcode_flat")
+    return out

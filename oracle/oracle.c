@@ -18,6 +18,8 @@
  *   oracle_depths     per-match dependency depth by byte-level simulation (§7.1)
  *   oracle_check      invariants: flattened sources are literal (§3.3), depth cap honoured (§7.4),
  *                     block depth fields equal the recomputed ones (§7.1)
+ *   oracle_transcode_flat  global chain flattening (§3.3) of an existing stream: every match rewritten as
+ *                     the maximal runs of its bytes with consecutive roots, each copying from its root
  *
  * Pins (tests/test_oracle_*.py): encode->decode round trip on every generator, agreement with the
  * textbook relative decoder, brute force over every legal parse of tiny strings, hand-assembled golden
@@ -42,6 +44,7 @@
 #define LONG_KEY 12
 #define PERIOD_MAX 16
 #define PERIOD_RESTART 32
+#define TRANSCODE_PERIOD_MAX 32  /* transcoder: repeats of at most this period restart from literal bytes */
 
 typedef struct {
     uint32_t block_log2, tile_log2, min_match, hash_bits, chain_limit, flatten, depth_cap, use_first, min_emit;
@@ -664,5 +667,91 @@ int oracle_check(const uint8_t *comp, uint64_t comp_len) {
     }
 done:
     free(r); free(L); free(s); free(lits); free(islit); free(wd);
+    return res;
+}
+
+/* ------------------------------------------------------------------------------------------ transcoding */
+/*
+ * Global chain flattening (§3.3) of an existing stream.  Every output byte has a root: a literal byte is
+ * its own root, and byte k of a match with destination d, source s and period p = d - s has the root of
+ * byte s + (k mod p) (which precedes d, so roots are settled in decode order).  Each match is rewritten
+ * as the maximal runs of its bytes whose roots are consecutive (root of byte k+1 = root of byte k, plus
+ * one); a run becomes a match copying from the root of its first byte when it is at least min_match long,
+ * else its bytes become literal bytes.  Self-overlapping matches (p < L) are taken first:
+ *   - one whose effective source [s, d) is all literal bytes already reads only literal bytes and stays;
+ *   - else, when its period is short (p <= 32) and L - p >= min_match, its first period [d, d + p) becomes
+ *     literal bytes and the rest a self-overlapping match (d + p, d, L - p) reading them (a repeat whose
+ *     source is not literal would otherwise break into a run per period);
+ *   - else it is split into runs like any other match.
+ * Every match of the result reads literal bytes only, so it has depth 1 (§7.1).
+ *
+ * The result keeps the input's block_log2, tile_log2 and min_match, has flatten mode 2 and depth cap 0,
+ * and decodes to the same bytes.  *out is malloc'ed; returns its length or a negative status (the input
+ * is validated by oracle_decode first).
+ */
+int64_t oracle_transcode_flat(const uint8_t *comp, uint64_t comp_len, uint8_t **out) {
+    *out = NULL;
+    or_info I;
+    int rc = oracle_peek(comp, comp_len, &I);
+    if (rc) return rc;
+    const uint64_t N = I.N, ns = I.n_seq;
+    uint8_t *x = (uint8_t *)malloc(N ? N : 1);
+    uint64_t *root = (uint64_t *)malloc((N ? N : 1) * 8);
+    uint64_t *r = (uint64_t *)malloc((ns ? ns : 1) * 8), *L = (uint64_t *)malloc((ns ? ns : 1) * 8),
+             *s = (uint64_t *)malloc((ns ? ns : 1) * 8);
+    mlist ml;
+    memset(&ml, 0, sizeof(ml));
+    int64_t res = OR_ERR_NOMEM;
+    if (!x || !root || !r || !L || !s) goto done;
+    rc = oracle_decode(comp, comp_len, x, N);
+    if (rc) { res = rc; goto done; }
+    {
+        const int64_t n = oracle_parse(comp, comp_len, r, L, s, NULL, ns);
+        if (n < 0) { res = n; goto done; }
+        /* roots, in decode order */
+        uint64_t pos = 0;
+        for (uint64_t i = 0; i < (uint64_t)n; i++) {
+            for (uint64_t j = 0; j < r[i]; j++) root[pos + j] = pos + j;
+            pos += r[i];
+            const uint64_t d = pos, p = d - s[i];
+            for (uint64_t k = 0; k < L[i]; k++) root[d + k] = root[s[i] + k % p];
+            pos += L[i];
+        }
+        /* the rewritten matches, in destination order */
+        pos = 0;
+        res = 0;
+        for (uint64_t i = 0; i < (uint64_t)n && !res; i++) {
+            pos += r[i];
+            const uint64_t d = pos, p = d - s[i], len = L[i];
+            pos += len;
+            if (!len) continue;
+            if (p < len) {
+                int lit_src = 1;
+                for (uint64_t j = 0; lit_src && j < p; j++) lit_src = root[s[i] + j] == s[i] + j;
+                if (lit_src) { res = ml_push(&ml, d, s[i], (uint32_t)len); continue; }
+                if (p <= TRANSCODE_PERIOD_MAX && len - p >= I.min_match) {
+                    res = ml_push(&ml, d + p, d, (uint32_t)(len - p));
+                    continue;
+                }
+            }
+            uint64_t k0 = 0;
+            for (uint64_t k = 1; k <= len && !res; k++) {
+                if (k < len && root[d + k] == root[d + k - 1] + 1) continue;
+                if (k - k0 >= I.min_match) res = ml_push(&ml, d + k0, root[d + k0], (uint32_t)(k - k0));
+                k0 = k;
+            }
+        }
+        if (res) goto done;
+        or_params prm;
+        memset(&prm, 0, sizeof(prm));
+        prm.block_log2 = I.block_log2;
+        prm.tile_log2 = I.tile_log2;
+        prm.min_match = I.min_match;
+        prm.flatten = 2;
+        res = oracle_serialize(x, N, ml.d, ml.s, ml.L, ml.n, &prm, out);
+    }
+done:
+    free(x); free(root); free(r); free(L); free(s);
+    ml_free(&ml);
     return res;
 }
