@@ -86,6 +86,8 @@ def stream_stats(comp: np.ndarray):
 MEASURED_TRAFFIC_PER_BYTE = {
     ("fastq-flat", "k_flat"): 2.6914,  # 440,329,728 + 282,149,120 bytes, 256 MiB flattened FASTQ, one k_flat launch
     ("text", "k_flow"): 7.1587,        # 1,504,913,408 + 416,750,592 bytes, 256 MiB deep text, one k_flow launch
+    ("batch", "k_flat"): 1.9065,       # 890,502,144 + 1,158,033,664 bytes, 512 streams of the batch (1,074,488,070
+                                       # decoded bytes), per k_flat launch (mean of 3)
 }
 
 

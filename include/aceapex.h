@@ -214,6 +214,35 @@ int aceapex_choose_device(const aceapex_info *info, const aceapex_device_model *
 /* Human-readable name of a status code. */
 const char *aceapex_strerror(int code);
 
+/* ---------------------------------------------------------------------------------------- transcoder */
+/*
+ * Global chain flattening of an existing stream (§3.3, applied after the fact; §7.1 orders the work): the
+ * result decodes to the same bytes and every one of its matches reads literal bytes only (depth 1), so the
+ * one-pass kernel decodes it.  Every match byte has a root, the literal byte it ultimately copies (a literal
+ * byte is its own root; byte k of a match with destination d, source s, period p = d - s has the root of
+ * byte s + (k mod p)).  Each match becomes: itself, if it overlaps itself and its effective source [s, d) is
+ * literal; else, for a short repeat (p < L, p <= 32, L - p >= min_match), its first period as literal bytes
+ * and the self-overlapping match (d + p, d, L - p); else the maximal runs of its bytes with consecutive
+ * roots, those of at least min_match bytes as matches from the root of their first byte, the rest as
+ * literal bytes.  The result keeps block_log2, tile_log2 and min_match, with flatten mode 2 and depth_cap 0.
+ *
+ * aceapex_transcode_create: comp is a device stream (16-byte aligned) of at most 2^32 - 1 decoded bytes.
+ *   Runs every step on the GPU (decode, roots, rewritten matches, block layout) and synchronizes `stream`;
+ *   *out_len receives the size of the result and *plan the object holding the intermediate device buffers
+ *   (about 4 bytes per decoded byte plus the wavefront workspace).  Returns the decode's status for a
+ *   malformed stream, ACEAPEX_ERR_SIZE for a stream over 2^32 - 1 bytes, ACEAPEX_ERR_NOMEM if a buffer
+ *   cannot be allocated (nothing is kept then).
+ * aceapex_transcode_write: writes the result into the device buffer out (16-byte aligned, out_cap >= out_len
+ *   bytes, else ACEAPEX_ERR_SIZE) on `stream` and synchronizes it.
+ * aceapex_transcode_info: matches and sequences of the result.
+ * aceapex_transcode_destroy: frees the plan (synchronizes the device).
+ */
+typedef struct aceapex_transcode aceapex_transcode;
+int aceapex_transcode_create(const void *comp, size_t comp_len, aceapex_transcode **plan, size_t *out_len, void *stream);
+int aceapex_transcode_write(aceapex_transcode *plan, void *out, size_t out_cap, void *stream);
+int aceapex_transcode_info(const aceapex_transcode *plan, uint64_t *n_match, uint64_t *n_seq);
+int aceapex_transcode_destroy(aceapex_transcode *plan);
+
 /* -------------------------------------------------------------------------------------------- server */
 /*
  * Continuous-batching decode server.  Requests are device-resident streams (16-byte aligned) with their

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libaceapex.so")
-_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp"]
+_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp", "transcode.cu"]
 _HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "warp_tile.cuh", "onepass.cuh", "wave.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -121,7 +121,8 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
            "aceapex_server_release", "aceapex_server_destroy",
-           "aceapex_encode", "aceapex_free", "aceapex_choose_device"]
+           "aceapex_encode", "aceapex_free", "aceapex_choose_device",
+           "aceapex_transcode_create", "aceapex_transcode_write", "aceapex_transcode_info", "aceapex_transcode_destroy"]
 
 _lib = None
 _lock = threading.Lock()
@@ -166,6 +167,10 @@ def lib():
             L.aceapex_server_poll.argtypes = [p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(p)]
             L.aceapex_server_release.argtypes = [p, ctypes.c_int64, p]
             L.aceapex_server_destroy.argtypes = [p]
+            L.aceapex_transcode_create.argtypes = [p, sz, ctypes.POINTER(p), ctypes.POINTER(sz), p]
+            L.aceapex_transcode_write.argtypes = [p, p, sz, p]
+            L.aceapex_transcode_info.argtypes = [p, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+            L.aceapex_transcode_destroy.argtypes = [p]
             L.aceapex_choose_device.argtypes = [ctypes.POINTER(Info), ctypes.POINTER(DeviceModel),
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.aceapex_encode.argtypes = [p, sz, ctypes.POINTER(EncParams), ctypes.POINTER(p)]
@@ -406,6 +411,51 @@ def choose_device(info: Info, cpu_gbps: float, link_gbps: float = 0.0, **model) 
     if rc < 0:
         raise AceapexError(rc, "aceapex_choose_device")
     return ("gpu" if rc == 1 else "cpu"), tc.value, tg.value
+
+
+class Transcode:
+    """Global chain flattening of a device-resident stream into a new stream whose matches all read literal
+    bytes, so that the one-pass kernel decodes it (aceapex_transcode_*; chain flattening §3.3 applied to an
+    existing stream).  Creating it runs the analysis on the GPU (decode, roots, rewritten matches, block
+    layout); write() serializes the new stream into a device buffer of at least out_len bytes."""
+
+    def __init__(self, comp, stream=None):
+        import torch
+        self._h = ctypes.c_void_p()
+        n = ctypes.c_size_t()
+        _check(lib().aceapex_transcode_create(comp.data_ptr(), comp.numel(), ctypes.byref(self._h), ctypes.byref(n),
+                                              _stream_ptr(stream)), "aceapex_transcode_create")
+        self.out_len = int(n.value)
+        nm, ns = ctypes.c_uint64(), ctypes.c_uint64()
+        lib().aceapex_transcode_info(self._h, ctypes.byref(nm), ctypes.byref(ns))
+        self.n_match, self.n_seq = int(nm.value), int(ns.value)
+
+    def write(self, out, stream=None) -> None:
+        _check(lib().aceapex_transcode_write(self._h, out.data_ptr(), out.numel(), _stream_ptr(stream)),
+               "aceapex_transcode_write")
+
+    def close(self) -> None:
+        if self._h:
+            lib().aceapex_transcode_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def transcode_flat(comp, stream=None):
+    """The globally flattened form of a device-resident stream, as a new uint8 device tensor."""
+    import torch
+    t = Transcode(comp, stream)
+    try:
+        out = torch.empty(max(t.out_len, 16), dtype=torch.uint8, device=comp.device)[:t.out_len]
+        t.write(out, stream)
+        return out
+    finally:
+        t.close()
 
 
 def set_wave_scheduler(kind: int) -> None:

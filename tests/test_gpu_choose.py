@@ -22,21 +22,29 @@ def test_both_choices_decode_exactly():
     cases = [("fastq", 24 << 20, dict(flatten=2, min_emit=12, long_bits=20, chain_limit=4)),   # large, shallow
              ("text", 3 << 20, dict(block_log2=12, tile_log2=8)),                              # deep chains
              ("rle7", 20_000, dict(flatten=2))]                                                # tiny
-    # measured CPU rate: the block-parallel decoder on all host cores
+    # measured CPU rate: the block-parallel decoder on all host cores (best of three, after a first call
+    # that loads the decoder)
     x0 = synth.make("text", 8 << 20, 1)
     c0 = oracle.encode(x0, flatten=2, min_emit=6)
-    t = time.perf_counter()
     assert oracle.cpupar_decode_rc(c0, threads=os.cpu_count())[0] == 0
-    cpu_gbps = x0.size / (time.perf_counter() - t) / 1e9
+    best = float("inf")
+    for _ in range(3):
+        t = time.perf_counter()
+        assert oracle.cpupar_decode_rc(c0, threads=os.cpu_count())[0] == 0
+        best = min(best, time.perf_counter() - t)
+    cpu_gbps = x0.size / best / 1e9
     picks = []
     for kind, n, kw in cases:
         x = synth.make(kind, n, 9)
         comp = oracle.encode(x, **kw)
         info = ax.peek_header(comp[:64])
         which, tc, tg = ax.choose_device(info, cpu_gbps)
+        assert which == ("gpu" if tg < tc else "cpu") and tc == pytest.approx(x.size / (cpu_gbps * 1e9))
         picks.append(which)
         rc, got = gpu_decode(comp, x.size)
         assert rc == 0 and np.array_equal(got, x), kind
         rc2, got2 = oracle.cpupar_decode_rc(comp, threads=os.cpu_count())
         assert rc2 == 0 and np.array_equal(got2, x), kind
-    assert picks[2] == "cpu"  # 20 KB: the fixed GPU overhead dominates
+    # 20 KB: the fixed GPU overhead (30 us) dominates at any CPU rate above 20 KB / 30 us
+    assert cpu_gbps < 0.7 or picks[2] == "cpu", cpu_gbps
+    assert picks[0] == "gpu", cpu_gbps  # 24 MiB one-pass: the GPU unless the host decodes at > 260 GB/s
