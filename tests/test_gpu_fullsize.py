@@ -87,3 +87,18 @@ def test_full_size_batch_graph_replay():
             del xs
     finally:
         plan.close()
+
+
+def test_full_size_text_transcode_matches_oracle():
+    """The 1 GiB deep text transcoded on the device into a globally flattened stream: byte-identical to the
+    oracle's transcode, and decoded exactly by the one-pass path."""
+    kind, n, seed, enc = FULL[0]
+    x, comp, _ = bench.cached_stream(kind, n, seed, enc)
+    got = ax.transcode_flat(torch.from_numpy(comp).cuda())
+    want = oracle.transcode_flat(comp)
+    assert got.numel() == want.size and np.array_equal(got.cpu().numpy(), want)
+    info = ax.peek_header(want[:64])
+    assert info.max_depth == 1
+    out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ax.decode(got, out)
+    assert torch.equal(out, torch.from_numpy(x).cuda())
