@@ -254,12 +254,12 @@ __device__ __forceinline__ void f4_mark(uint32_t *lbm, uint32_t ib, uint32_t n) 
 }
 
 // Bits [a, b) (a < b) of a bit array all set: GLOB reads the array through L2 (written by other warps of
-// this launch), else from shared memory.
+// this launch), else from shared memory.  Bit positions are stream positions, below kF4MaxN < 2^32.
 template <bool GLOB>
-__device__ __forceinline__ bool f4_bits(const uint32_t *w, uint64_t a, uint64_t b) {
-    const uint64_t q0 = a >> 5, q1 = (b - 1) >> 5;
+__device__ __forceinline__ bool f4_bits(const uint32_t *w, uint32_t a, uint32_t b) {
+    const uint32_t q0 = a >> 5, q1 = (b - 1) >> 5;
     bool ok = true;
-    for (uint64_t q = q0; q <= q1 && ok; q++) {
+    for (uint32_t q = q0; q <= q1 && ok; q++) {
         const uint32_t lo = q == q0 ? (uint32_t)(a & 31u) : 0u, hi = q == q1 ? (uint32_t)((b - 1) & 31u) + 1 : 32u;
         const uint32_t m = __funnelshift_lc(0xFFFFFFFFu, 0u, hi) & ~__funnelshift_lc(0xFFFFFFFFu, 0u, lo);
         const uint32_t v = GLOB ? __ldcg(w + q) : w[q];
@@ -270,7 +270,7 @@ __device__ __forceinline__ bool f4_bits(const uint32_t *w, uint64_t a, uint64_t 
 
 // ------------------------------------------------------------------------------------------ kernel
 template <int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_flat(WsHead *head, StreamState *sst, uint32_t *flags,
+__global__ void __launch_bounds__(32 * WARPS, 20 / WARPS) k_flat(WsHead *head, StreamState *sst, uint32_t *flags,
                                                          const StreamDesc *descs, LaunchArgs a) {
     extern __shared__ uint4 dyn_smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -545,15 +545,34 @@ __global__ void __launch_bounds__(32 * WARPS) k_flat(WsHead *head, StreamState *
                     }
                     WPHASE(4);
                     // every source byte read must be a literal byte: this tile's part against the bits in
-                    // shared memory, earlier tiles' against the published bits in HBM
+                    // shared memory, earlier tiles' against the published bits in HBM (one or two words loaded
+                    // directly, longer ranges word by word).  32-bit stream positions: the source range ends at
+                    // or before b0 + d < kF4MaxN.
+                    const uint32_t tile_abs = (uint32_t)(c.b0 + lo);
+                    const uint32_t ra = wrap ? s : s + k0, rb = wrap ? b0 + d : s + k0 + len;
+                    const uint32_t rg = rb < tile_abs ? rb : tile_abs;
+                    uint32_t gv0 = 0, gv1 = 0, gm0 = 0, gm1 = 0;
+                    bool glong = false;
+                    if (len && ra < rg) {
+                        const uint32_t q0 = ra >> 5, q1 = (rg - 1) >> 5;
+                        const uint32_t lo0 = ra & 31u, hi1 = ((rg - 1) & 31u) + 1u;
+                        if (q1 == q0) {
+                            gm0 = __funnelshift_lc(kFull, 0u, hi1) & ~__funnelshift_lc(kFull, 0u, lo0);
+                            gv0 = __ldcg(sd.litmap + q0);
+                        } else if (q1 == q0 + 1) {
+                            gm0 = ~__funnelshift_lc(kFull, 0u, lo0);
+                            gm1 = __funnelshift_lc(kFull, 0u, hi1);
+                            gv0 = __ldcg(sd.litmap + q0);
+                            gv1 = __ldcg(sd.litmap + q1);
+                        } else {
+                            glong = true;
+                        }
+                    }
                     if (len) {
-                        const uint64_t tile_abs = c.b0 + lo;
-                        const uint64_t ra = wrap ? s : (uint64_t)s + k0;
-                        const uint64_t rb = wrap ? (uint64_t)b0 + d : (uint64_t)s + k0 + len;
-                        const uint64_t rg = rb < tile_abs ? rb : tile_abs;
-                        bool lit = ra >= rg || f4_bits<true>(sd.litmap, ra, rg);
+                        bool lit = (gv0 & gm0) == gm0 && (gv1 & gm1) == gm1;
+                        if (glong) lit = f4_bits<true>(sd.litmap, ra, rg);
                         if (lit && rb > tile_abs) {
-                            const uint64_t a2 = ra > tile_abs ? ra : tile_abs;
+                            const uint32_t a2 = ra > tile_abs ? ra : tile_abs;
                             lit = f4_bits<false>(W.lbm, a2 - tile_abs + ishift, rb - tile_abs + ishift);
                         }
                         if (!lit) report_depth(st);
