@@ -43,11 +43,16 @@ class Info(ctypes.Structure):
                [(n, ctypes.c_uint32) for n in ("block_log2", "tile_log2", "min_match", "flatten", "depth_cap", "max_depth")]
 
 
+_ENT_SRC = os.path.join(_HERE, "entropy.c")
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (plain gcc -O2), and the block-parallel CPU decoder."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    """Compile oracle.c and entropy.c into liboracle.so next to them (plain gcc -O2), and the block-parallel
+    CPU decoder."""
+    srcs = [_SRC, _ENT_SRC]
+    if force or not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(p) for p in srcs):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp] + srcs)
         os.replace(tmp, _LIB_PATH)
     build_cpupar(force)
     return _LIB_PATH
@@ -108,6 +113,14 @@ def _load():
             lib.oracle_depths.argtypes = [p, u64, p, u64]
             lib.oracle_depths.restype = i64
             lib.oracle_check.argtypes = [p, u64]
+            lib.oracle_huff_lengths.argtypes = [p, p]
+            lib.oracle_huff_lengths.restype = ctypes.c_int
+            lib.oracle_entropy_encode.argtypes = [p, u64, pp]
+            lib.oracle_entropy_encode.restype = i64
+            lib.oracle_entropy_peek.argtypes = [p, u64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_entropy_peek.restype = ctypes.c_int
+            lib.oracle_entropy_decode.argtypes = [p, u64, p, u64]
+            lib.oracle_entropy_decode.restype = ctypes.c_int
             lib.oracle_transcode_flat.restype = ctypes.c_int64
             lib.oracle_transcode_flat.argtypes = [p, u64, pp]
             lib.oracle_check.restype = ctypes.c_int
@@ -249,4 +262,44 @@ def transcode_flat(comp) -> np.ndarray:
     rc, out = transcode_flat_rc(comp)
     if rc:
         raise OracleError(rc, "oracle_transcode_flat")
+    return out
+
+
+def huff_lengths(counts) -> np.ndarray:
+    """Code lengths (at most 12) of the entropy container's code for 256 symbol counts."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    assert c.size == 256
+    out = np.zeros(256, dtype=np.uint8)
+    _load().oracle_huff_lengths(c.ctypes.data, out.ctypes.data)
+    return out
+
+
+def entropy_encode(raw) -> np.ndarray:
+    """Wrap a stream in the entropy container (format §6)."""
+    a = _u8(raw)
+    ptr = ctypes.c_void_p()
+    n = _load().oracle_entropy_encode(a.ctypes.data, a.size, ctypes.byref(ptr))
+    if n < 0:
+        raise OracleError(n, "oracle_entropy_encode")
+    return _take(ptr, n)
+
+
+def entropy_decode_rc(e, raw_len: int | None = None):
+    """(status, wrapped stream or None) of an entropy container."""
+    c = _u8(e)
+    if raw_len is None:
+        rl, ns = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = _load().oracle_entropy_peek(c.ctypes.data, c.size, ctypes.byref(rl), ctypes.byref(ns))
+        if rc:
+            return rc, None
+        raw_len = int(rl.value)
+    out = np.zeros(max(raw_len, 1), dtype=np.uint8)
+    rc = _load().oracle_entropy_decode(c.ctypes.data, c.size, out.ctypes.data, raw_len)
+    return rc, (out[:raw_len] if rc == 0 else None)
+
+
+def entropy_decode(e) -> np.ndarray:
+    rc, out = entropy_decode_rc(e)
+    if rc:
+        raise OracleError(rc, "oracle_entropy_decode")
     return out
