@@ -214,6 +214,33 @@ int aceapex_choose_device(const aceapex_info *info, const aceapex_device_model *
 /* Human-readable name of a status code. */
 const char *aceapex_strerror(int code);
 
+/* ------------------------------------------------------------------------------------- entropy stage */
+/*
+ * Entropy container (stream format §6): the entropy stage the paper names without fixing one (§6 of the
+ * paper, an FSE stage over the arrays), read here as canonical Huffman coding (codes of at most 12 bits) of
+ * segments of at most 4096 bytes of a stream, 32 interleaved lanes per segment; decoding it gives back the
+ * wrapped stream byte for byte, which the decode calls above then take.
+ *
+ * aceapex_entropy_peek: the container header from host memory (len >= 64 bytes): ACEAPEX_ERR_FORMAT for a
+ *   bad magic/version/field, ACEAPEX_ERR_SIZE for a bad e_len.
+ * aceapex_entropy_decode: decodes the device container e (16-byte aligned, e_len bytes, header info from
+ *   aceapex_entropy_peek of its first 64 bytes) into the device buffer raw (raw_len = info->raw_len bytes),
+ *   enqueued on `stream` without a host synchronization; *d_status (device int32) receives 0 or
+ *   ACEAPEX_ERR_FORMAT (any malformed segment, table, length, Kraft sum or bitstream).  Returns
+ *   ACEAPEX_ERR_ARG / ACEAPEX_ERR_SIZE for bad arguments, ACEAPEX_ERR_CUDA if the launch fails.  It uses no
+ *   workspace; one launch, one warp per segment.
+ */
+typedef struct {
+    uint64_t raw_len, n_seg, e_len;
+} aceapex_entropy_info;
+int aceapex_entropy_peek(const void *host_prefix, size_t len, aceapex_entropy_info *info);
+/* Wrap the host stream raw (raw_len bytes) in an entropy container, on the host: stored stream header, block
+ * index, block headers and sync tables; each block section coded with its own code (a segment stored when
+ * coding would not shrink it).  *out is allocated (release with aceapex_free), *out_len its length. */
+int aceapex_entropy_encode(const void *raw, size_t raw_len, void **out, size_t *out_len);
+int aceapex_entropy_decode(const void *e, size_t e_len, const aceapex_entropy_info *info, void *raw, size_t raw_len,
+                           int32_t *d_status, void *stream);
+
 /* ---------------------------------------------------------------------------------------- transcoder */
 /*
  * Global chain flattening of an existing stream (§3.3, applied after the fact; §7.1 orders the work): the

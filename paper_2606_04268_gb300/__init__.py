@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libaceapex.so")
-_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp", "transcode.cu"]
+_SOURCES = ["decode.cu", "api.cpp", "encoder.cpp", "serve.cpp", "transcode.cu", "entropy.cu", "entropy_enc.cpp"]
 _HEADERS = ["decode.h", "layout.h", "device_common.cuh", "tile.cuh", "warp_tile.cuh", "onepass.cuh", "wave.cuh"]
 NVCC_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -101,6 +101,10 @@ class Stats(ctypes.Structure):
                [("level_hist", ctypes.c_uint64 * HIST_MAX), ("phase_cycles", ctypes.c_uint64 * 8)]
 
 
+class EntropyInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("raw_len", "n_seg", "e_len")]
+
+
 class DeviceModel(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("cpu_gbps", "gpu_one_pass_gbps", "gpu_wave_gbps", "gpu_level_us", "gpu_fixed_us", "link_gbps")]
@@ -122,7 +126,8 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
            "aceapex_server_release", "aceapex_server_destroy",
            "aceapex_encode", "aceapex_free", "aceapex_choose_device",
-           "aceapex_transcode_create", "aceapex_transcode_write", "aceapex_transcode_info", "aceapex_transcode_destroy"]
+           "aceapex_transcode_create", "aceapex_transcode_write", "aceapex_transcode_info", "aceapex_transcode_destroy",
+           "aceapex_entropy_peek", "aceapex_entropy_decode", "aceapex_entropy_encode"]
 
 _lib = None
 _lock = threading.Lock()
@@ -167,6 +172,9 @@ def lib():
             L.aceapex_server_poll.argtypes = [p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(p)]
             L.aceapex_server_release.argtypes = [p, ctypes.c_int64, p]
             L.aceapex_server_destroy.argtypes = [p]
+            L.aceapex_entropy_peek.argtypes = [p, sz, ctypes.POINTER(EntropyInfo)]
+            L.aceapex_entropy_encode.argtypes = [p, sz, ctypes.POINTER(p), ctypes.POINTER(sz)]
+            L.aceapex_entropy_decode.argtypes = [p, sz, ctypes.POINTER(EntropyInfo), p, sz, p, p]
             L.aceapex_transcode_create.argtypes = [p, sz, ctypes.POINTER(p), ctypes.POINTER(sz), p]
             L.aceapex_transcode_write.argtypes = [p, p, sz, p]
             L.aceapex_transcode_info.argtypes = [p, ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -411,6 +419,46 @@ def choose_device(info: Info, cpu_gbps: float, link_gbps: float = 0.0, **model) 
     if rc < 0:
         raise AceapexError(rc, "aceapex_choose_device")
     return ("gpu" if rc == 1 else "cpu"), tc.value, tg.value
+
+
+def entropy_encode(raw) -> np.ndarray:
+    """Wrap a host stream in the entropy container with the library's CPU encoder (aceapex_entropy_encode)."""
+    a = np.ascontiguousarray(raw, dtype=np.uint8)
+    ptr, n = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(lib().aceapex_entropy_encode(a.ctypes.data if a.size else None, a.size, ctypes.byref(ptr), ctypes.byref(n)),
+           "aceapex_entropy_encode")
+    out = np.empty(n.value, np.uint8)
+    ctypes.memmove(out.ctypes.data, ptr, n.value)
+    lib().aceapex_free(ptr)
+    return out
+
+
+def entropy_peek(host_prefix) -> EntropyInfo:
+    """Header of an entropy container (aceapex_entropy_peek) from its first 64 bytes in host memory."""
+    b = np.ascontiguousarray(np.asarray(host_prefix, dtype=np.uint8)[:64])
+    info = EntropyInfo()
+    _check(lib().aceapex_entropy_peek(b.ctypes.data, b.size, ctypes.byref(info)), "aceapex_entropy_peek")
+    return info
+
+
+def entropy_decode_async(e, info: EntropyInfo, raw, status, stream=None) -> None:
+    """Enqueue the decode of the device entropy container e into the device buffer raw (the wrapped stream);
+    status: device int32 tensor receiving 0 or ERR_FORMAT."""
+    _check(lib().aceapex_entropy_decode(e.data_ptr(), e.numel(), ctypes.byref(info), raw.data_ptr(), raw.numel(),
+                                        status.data_ptr(), _stream_ptr(stream)), "aceapex_entropy_decode")
+
+
+def entropy_decode(e, stream=None):
+    """The wrapped stream of a device entropy container, as a new uint8 device tensor (blocking)."""
+    import torch
+    info = entropy_peek(e[:64].cpu().numpy())
+    raw = torch.empty(max(int(info.raw_len), 16), dtype=torch.uint8, device=e.device)[:int(info.raw_len)]
+    status = torch.zeros(1, dtype=torch.int32, device=e.device)
+    entropy_decode_async(e, info, raw, status, stream)
+    st = int(status.item())
+    if st:
+        raise AceapexError(st, "aceapex_entropy_decode")
+    return raw
 
 
 class Transcode:

@@ -568,8 +568,11 @@ __global__ void __launch_bounds__(32 * WARPS, 20 / WARPS) k_flat(WsHead *head, S
                             glong = true;
                         }
                     }
+                    const bool lit_glob = (gv0 & gm0) == gm0 && (gv1 & gm1) == gm1;
+                    const uint32_t first = len < 16 ? len : 16u;
+                    if (first) f4_match_piece(imgw, ib, sd.out, s, p, k0, first, wrap);
                     if (len) {
-                        bool lit = (gv0 & gm0) == gm0 && (gv1 & gm1) == gm1;
+                        bool lit = lit_glob;
                         if (glong) lit = f4_bits<true>(sd.litmap, ra, rg);
                         if (lit && rb > tile_abs) {
                             const uint32_t a2 = ra > tile_abs ? ra : tile_abs;
@@ -577,8 +580,6 @@ __global__ void __launch_bounds__(32 * WARPS, 20 / WARPS) k_flat(WsHead *head, S
                         }
                         if (!lit) report_depth(st);
                     }
-                    const uint32_t first = len < 16 ? len : 16u;
-                    if (first) f4_match_piece(imgw, ib, sd.out, s, p, k0, first, wrap);
                     const uint32_t extra = len > 16 ? (len - 1) >> 4 : 0u;
                     if (__any_sync(kFull, extra != 0)) {
                         uint32_t ex = extra;
