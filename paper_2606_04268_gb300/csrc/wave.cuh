@@ -314,11 +314,8 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
                 ready = !(w < m && __ldg(&wb.mdst[w]) < send);
             }
             if (__any_sync(mask, ready)) {
-                // a match of at most 32 bytes (16 when it overlaps itself) is copied by its lane; longer ones by
-                // the whole warp, 16 bytes per lane at a time, or byte k from s + (k mod p) when self-overlapping
-                const uint64_t p = d - s;
-                const bool longm = ready && (p < L ? L > 16 : L > 32);
-                if (ready && !longm) {
+                if (ready) {
+                    const uint64_t p = d - s;
                     if (p >= L) {
                         for (uint64_t o = 0; o < L; o += 16)
                             lane_copy_out(out, d + o, s + o, (uint32_t)(L - o < 16 ? L - o : 16));
@@ -329,24 +326,6 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
                             if (++km == (uint32_t)p) km = 0;
                         }
                     }
-                }
-                unsigned lm = __ballot_sync(mask, longm);
-                while (lm) {
-                    const int o = __ffs(lm) - 1;
-                    lm &= lm - 1;
-                    const uint64_t od = __shfl_sync(mask, d, o), os = __shfl_sync(mask, s, o);
-                    const uint32_t oL = (uint32_t)__shfl_sync(mask, L, o);
-                    if (od - os >= oL) {
-                        for (uint32_t off = 16 * sub; off < oL; off += 16 * G)
-                            lane_copy_out(out, od + off, os + off, oL - off < 16 ? oL - off : 16u);
-                    } else {
-                        const uint32_t op = (uint32_t)(od - os);  // below oL
-                        for (uint32_t k = sub; k < oL; k += G) out[od + k] = __ldcg(out + os + k % op);
-                    }
-                }
-                __syncwarp(mask);  // the bytes of the long matches, written by all lanes, before their depths
-                if (ready) {
-                    if (longm) __threadfence();
                     uint32_t dep = mx + 1;
                     // a match deeper than its block's max_depth field: the stream understates its depth
                     if (L && dep > wb.bdepth[d >> sd.block_log2]) report_depth(&sst[0]);
