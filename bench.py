@@ -505,6 +505,25 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     hbm_peak, peak_kind = peaks()
+    if args.entropy:
+        # the stream in the entropy container: a step is the GPU entropy decode plus the decode
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            r = measure_entropy(ax, torch, x, comp, args.steps, args.warmup, hbm_peak, peak_kind, barrier)
+        ms = max_over_ranks(r["ms"], world, "cuda")
+        if rank != 0:
+            torch.distributed.destroy_process_group()
+            return
+        line = _base_line(args, x.size * world / (ms * 1e-3) / 1e9, ms, desc + ", in the entropy container",
+                          {k: v for k, v in single_config(args, world).items() if k != "workload"})
+        line["details"] = {k: r[k] for k in ("ratio", "ratio_without_entropy", "entropy_ms", "n_segments", "encode_s")}
+        line["decode_roofline_frac"] = r["decode_roofline_frac"]
+        line["roofline"] = r["entropy_roofline"]
+        line["gpu_launches"] = None
+        line["clocks"] = clk.summary()
+        print(json.dumps(line), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     with ClockSampler(torch.cuda.current_device()) as clk:
         r = measure_stream(ax, torch, x, comp, args.steps, args.warmup, hbm_peak, peak_kind, args.workload, barrier)
     ms = max_over_ranks(r["ms"], world, "cuda")
@@ -807,8 +826,9 @@ def measure_entropy(ax, torch, x, comp, steps, warmup, hbm_peak, peak_kind, barr
     ms = e0.elapsed_time(e1) / steps
     barrier()
     e0.record(stream)
-    for _ in range(steps):
-        ax.entropy_decode_async(d_e, einfo, raw, st[0:1], stream)
+    with nvtx_range("profiled-steps"):
+        for _ in range(steps):
+            ax.entropy_decode_async(d_e, einfo, raw, st[0:1], stream)
     e1.record(stream)
     barrier()
     ent_ms = e0.elapsed_time(e1) / steps
@@ -1047,6 +1067,8 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="batch workload: skip the single-stream configurations measured beside it")
     ap.add_argument("--size", type=int, default=0, help="override the workload size (bytes)")
+    ap.add_argument("--entropy", action="store_true",
+                    help="single-stream workloads: the stream in the entropy container (GPU entropy decode + decode)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-all-cores", action="store_true",
