@@ -84,9 +84,9 @@ def stream_stats(comp: np.ndarray):
 # of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / decoded bytes),
 # scaled to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
 MEASURED_TRAFFIC_PER_BYTE = {
-    ("fastq-flat", "k_flat"): 2.6914,  # 440,329,728 + 282,149,120 bytes, 256 MiB flattened FASTQ, one k_flat launch
-    ("text", "k_flow"): 7.1587,        # 1,504,913,408 + 416,750,592 bytes, 256 MiB deep text, one k_flow launch
-    ("batch", "k_flat"): 1.9065,       # 890,502,144 + 1,158,033,664 bytes, 512 streams of the batch (1,074,488,070
+    ("fastq-flat", "k_flat"): 2.6845,  # 439,158,016 + 281,489,152 bytes, 256 MiB flattened FASTQ, one k_flat launch
+    ("text", "k_flow"): 7.1578,        # 1,504,972,800 + 416,439,552 bytes, 256 MiB deep text, one k_flow launch
+    ("batch", "k_flat"): 1.9065,       # 890,452,053 + 1,158,055,339 bytes, 512 streams of the batch (1,074,488,070
                                        # decoded bytes), per k_flat launch (mean of 3)
 }
 

@@ -23,11 +23,14 @@ constexpr uint32_t kESeg = 4096;      // bytes of the wrapped stream per segment
 constexpr uint32_t kEMaxLen = 12;     // longest code
 constexpr int kEWarps = 4;            // warps per CTA
 
+constexpr uint32_t kEStage = 8 + 128 + 64 + kESeg;  // payloads up to this size are staged in shared memory
+
 struct alignas(16) EWarp {
     uint16_t tbl[1u << kEMaxLen];     // 12-bit prefix -> symbol | length << 8 (0: no code)
     uint16_t code[256];
     uint8_t len[256];
     uint32_t running[kEMaxLen + 1];
+    alignas(16) uint8_t pay[kEStage]; // the segment's payload (16-byte copies), when it fits
 };
 
 __device__ __forceinline__ uint64_t e_ld64(const uint8_t *p) {  // 8-aligned
@@ -129,7 +132,14 @@ __global__ void __launch_bounds__(32 * kEWarps) k_entropy(const uint8_t *e, uint
         if ((h >> 8) || mode > 1) { if (lane == 0) e_fail(status); return; }
         if (mode == 0) {
             if (table != 0 || P < 8 + (uint64_t)n) { if (lane == 0) e_fail(status); return; }
-            for (uint32_t j = lane; j < n; j += 32) raw[ro + j] = __ldg(q + 8 + j);
+            if ((ro & 7) == 0) {  // 8-byte words (the payload's bytes start 8-aligned), then the tail
+                const unsigned long long *src = reinterpret_cast<const unsigned long long *>(q + 8);
+                unsigned long long *dst = reinterpret_cast<unsigned long long *>(raw + ro);
+                for (uint32_t i = lane; i < n / 8; i += 32) dst[i] = __ldg(src + i);
+                for (uint32_t j = (n & ~7u) + lane; j < n; j += 32) raw[ro + j] = __ldg(q + 8 + j);
+            } else {
+                for (uint32_t j = lane; j < n; j += 32) raw[ro + j] = __ldg(q + 8 + j);
+            }
             continue;
         }
         if (table > k) { if (lane == 0) e_fail(status); return; }
@@ -150,12 +160,24 @@ __global__ void __launch_bounds__(32 * kEWarps) k_entropy(const uint8_t *e, uint
         const uint32_t total = __shfl_sync(0xffffffffu, start, 31);
         start -= nbytes;
         if (P < lb_at + 64 + total) { if (lane == 0) e_fail(status); return; }
-        const uint8_t *p = q + lb_at + 64 + start, *pe = p + nbytes;
+        // the bitstreams are read from shared memory when the payload fits there (one 16-byte copy per lane
+        // per step), else straight from the container
+        const uint8_t *p, *pe;
+        if (P <= kEStage) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(q);
+            uint4 *dst = reinterpret_cast<uint4 *>(W.pay);
+            for (uint32_t i = lane; i < (uint32_t)(P >> 4); i += 32) dst[i] = __ldg(src + i);
+            __syncwarp();
+            p = W.pay + lb_at + 64 + start;
+        } else {
+            p = q + lb_at + 64 + start;
+        }
+        pe = p + nbytes;
         uint64_t buf = 0;
         uint32_t nb = 0;
         bool bad = false;
         for (uint32_t j = lane; j < n; j += 32) {
-            while (nb <= 56 && p < pe) { buf |= (uint64_t)__ldg(p++) << (56 - nb); nb += 8; }
+            while (nb <= 56 && p < pe) { buf |= (uint64_t)(*p++) << (56 - nb); nb += 8; }
             const uint32_t ent = W.tbl[buf >> (64 - kEMaxLen)], L = ent >> 8;
             if (L == 0 || L > nb) { bad = true; break; }
             raw[ro + j] = (uint8_t)ent;
@@ -163,6 +185,7 @@ __global__ void __launch_bounds__(32 * kEWarps) k_entropy(const uint8_t *e, uint
             nb -= L;
         }
         if (__any_sync(0xffffffffu, bad)) { if (lane == 0) e_fail(status); return; }
+        __syncwarp();  // the staged payload is read by every lane before the next segment overwrites it
     }
 }
 
