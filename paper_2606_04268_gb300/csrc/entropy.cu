@@ -30,7 +30,8 @@ struct alignas(16) EWarp {
     uint16_t code[256];
     uint8_t len[256];
     uint32_t running[kEMaxLen + 1];
-    alignas(16) uint8_t pay[kEStage]; // the segment's payload (16-byte copies), when it fits
+    alignas(16) uint8_t pay[kEStage + 16];  // the segment's payload (16-byte copies), when it fits; the
+                                            // 16 spare bytes keep a two-word read at the end inside
 };
 
 __device__ __forceinline__ uint64_t e_ld64(const uint8_t *p) {  // 8-aligned
@@ -160,29 +161,47 @@ __global__ void __launch_bounds__(32 * kEWarps) k_entropy(const uint8_t *e, uint
         const uint32_t total = __shfl_sync(0xffffffffu, start, 31);
         start -= nbytes;
         if (P < lb_at + 64 + total) { if (lane == 0) e_fail(status); return; }
-        // the bitstreams are read from shared memory when the payload fits there (one 16-byte copy per lane
-        // per step), else straight from the container
-        const uint8_t *p, *pe;
+        bool bad = false;
         if (P <= kEStage) {
+            // the payload in shared memory (one 16-byte copy per lane per step); the next 12 bits of a lane are
+            // read from the two big-endian words around its bit position
             const uint4 *src = reinterpret_cast<const uint4 *>(q);
             uint4 *dst = reinterpret_cast<uint4 *>(W.pay);
             for (uint32_t i = lane; i < (uint32_t)(P >> 4); i += 32) dst[i] = __ldg(src + i);
             __syncwarp();
-            p = W.pay + lb_at + 64 + start;
+            const uint32_t *wd = reinterpret_cast<const uint32_t *>(W.pay);
+            uint32_t bit = 8 * (uint32_t)(lb_at + 64 + start);
+            const uint32_t bit_end = bit + 8 * nbytes;
+            // words idx and idx + 1 of the payload (big-endian) hold the next bits; a code is at most 12 bits,
+            // so the window moves by at most one word per code
+            uint32_t idx = bit >> 5;
+            uint32_t w0 = __byte_perm(wd[idx], 0, 0x0123), w1 = __byte_perm(wd[idx + 1], 0, 0x0123);
+            uint8_t *dst_b = raw + ro + lane;
+            for (uint32_t j = lane; j < n; j += 32, dst_b += 32) {
+                const uint32_t peek = __funnelshift_l(w1, w0, bit & 31u);
+                const uint32_t ent = W.tbl[peek >> (32 - kEMaxLen)], L = ent >> 8;
+                if (L == 0 || bit + L > bit_end) { bad = true; break; }
+                *dst_b = (uint8_t)ent;
+                bit += L;
+                if ((bit >> 5) != idx) {
+                    idx++;
+                    w0 = w1;
+                    w1 = __byte_perm(wd[idx + 1], 0, 0x0123);
+                }
+            }
         } else {
-            p = q + lb_at + 64 + start;
-        }
-        pe = p + nbytes;
-        uint64_t buf = 0;
-        uint32_t nb = 0;
-        bool bad = false;
-        for (uint32_t j = lane; j < n; j += 32) {
-            while (nb <= 56 && p < pe) { buf |= (uint64_t)(*p++) << (56 - nb); nb += 8; }
-            const uint32_t ent = W.tbl[buf >> (64 - kEMaxLen)], L = ent >> 8;
-            if (L == 0 || L > nb) { bad = true; break; }
-            raw[ro + j] = (uint8_t)ent;
-            buf <<= L;
-            nb -= L;
+            // straight from the container, a byte at a time
+            const uint8_t *p = q + lb_at + 64 + start, *pe = p + nbytes;
+            uint64_t buf = 0;
+            uint32_t nb = 0;
+            for (uint32_t j = lane; j < n; j += 32) {
+                while (nb <= 56 && p < pe) { buf |= (uint64_t)__ldg(p++) << (56 - nb); nb += 8; }
+                const uint32_t ent = W.tbl[buf >> (64 - kEMaxLen)], L = ent >> 8;
+                if (L == 0 || L > nb) { bad = true; break; }
+                raw[ro + j] = (uint8_t)ent;
+                buf <<= L;
+                nb -= L;
+            }
         }
         if (__any_sync(0xffffffffu, bad)) { if (lane == 0) e_fail(status); return; }
         __syncwarp();  // the staged payload is read by every lane before the next segment overwrites it
