@@ -157,6 +157,9 @@ int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *com
                               const size_t *out_lens, void *stream, aceapex_batch_plan **plan);
 int aceapex_batch_plan_launch(aceapex_batch_plan *plan, int graph, void *stream);
 int aceapex_batch_plan_statuses(aceapex_batch_plan *plan, int32_t *statuses, void *stream);
+/* The same statuses written to the device array d_statuses (n int32), enqueued on `stream` after the
+ * plan's launch, with no host synchronization (the device-status form of the batch decode). */
+int aceapex_batch_plan_statuses_device(aceapex_batch_plan *plan, int32_t *d_statuses, void *stream);
 int aceapex_batch_plan_destroy(aceapex_batch_plan *plan);
 
 /* Launch shape of the one-pass kernel: warps per CTA (2, 4 or 8; default 4) and CTAs per SM (0 = as many as

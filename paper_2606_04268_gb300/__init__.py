@@ -120,7 +120,7 @@ class EncParams(ctypes.Structure):
 SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "aceapex_decode_async",
            "aceapex_decode_noalloc",
            "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
-           "aceapex_batch_plan_statuses", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
+           "aceapex_batch_plan_statuses", "aceapex_batch_plan_statuses_device", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
            "aceapex_decode_host", "aceapex_get_launch_config", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
@@ -153,6 +153,7 @@ def lib():
             L.aceapex_batch_plan_launch.argtypes = [p, i32, p]
             L.aceapex_batch_plan_statuses.argtypes = [p, p, p]
             L.aceapex_batch_plan_destroy.argtypes = [p]
+            L.aceapex_batch_plan_statuses_device.argtypes = [p, p, p]
             L.aceapex_set_launch_config.argtypes = [i32, i32]
             L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 2
             L.aceapex_set_force_wavefront.argtypes = [i32]
@@ -313,6 +314,11 @@ class BatchPlan:
         st = np.zeros(max(self.n, 1), np.int32)
         lib().aceapex_batch_plan_statuses(self._h, st.ctypes.data, _stream_ptr(stream))
         return st[:self.n]
+
+    def statuses_device(self, out, stream=None) -> None:
+        """Write the per-stream statuses into the device int32 tensor out (stream-ordered, no host sync)."""
+        _check(lib().aceapex_batch_plan_statuses_device(self._h, out.data_ptr(), _stream_ptr(stream)),
+               "aceapex_batch_plan_statuses_device")
 
     def close(self) -> None:
         if self._h:

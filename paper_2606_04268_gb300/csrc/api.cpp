@@ -399,6 +399,7 @@ struct aceapex_batch_plan {
     uint8_t *wave_ws = nullptr;            // shared by the wave streams, decoded one after another
     size_t wave_cap = 0;
     int32_t *wave_status = nullptr;        // one device status per wave stream
+    int32_t *status_map = nullptr;         // device, 2 per stream: where its status comes from (plan_statuses_device)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
 };
@@ -494,10 +495,29 @@ int aceapex_batch_plan_create(int n, const void *const *comps, const size_t *com
         }
         cudaMemsetAsync(P->wave_ws, 0, wave_need, stream);
     }
-    cudaError_t e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) { cudaFree(P->ws); cudaFree(P->wave_ws); cudaFree(P->wave_status); delete P; return cuda_fail(e); }
+    // per stream: (0, status known on the host) | (1, index among the one-pass streams) | (2, index among the
+    // wavefront streams), for the stream-ordered status gather
+    std::vector<int32_t> map(2 * (size_t)std::max(n, 1), 0);
+    for (int i = 0; i < n; i++) map[2 * i + 1] = P->arg_status[i];
+    for (size_t k = 0; k < P->flat_idx.size(); k++) { map[2 * P->flat_idx[k]] = 1; map[2 * P->flat_idx[k] + 1] = (int32_t)k; }
+    for (size_t k = 0; k < P->wave_idx.size(); k++) { map[2 * P->wave_idx[k]] = 2; map[2 * P->wave_idx[k] + 1] = (int32_t)k; }
+    cudaError_t e = cudaMalloc((void **)&P->status_map, 4 * map.size());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->status_map, map.data(), 4 * map.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(P->ws); cudaFree(P->wave_ws); cudaFree(P->wave_status); cudaFree(P->status_map);
+        delete P;
+        return cuda_fail(e);
+    }
     *plan_out = P;
     return kOK;
+}
+
+int aceapex_batch_plan_statuses_device(aceapex_batch_plan *P, int32_t *d_statuses, void *stream_) {
+    if (!P || (!d_statuses && P->n)) return kErrArg;
+    if (P->n == 0) return kOK;
+    return cuda_fail(launch_gather_status(P->n, P->status_map, (const int32_t *)(P->ws + P->flat_L.status),
+                                          P->wave_status, d_statuses, (cudaStream_t)stream_));
 }
 
 static int plan_enqueue(aceapex_batch_plan *P, cudaStream_t stream) {
@@ -575,6 +595,7 @@ int aceapex_batch_plan_destroy(aceapex_batch_plan *P) {
     cudaFree(P->ws);
     cudaFree(P->wave_ws);
     cudaFree(P->wave_status);
+    cudaFree(P->status_map);
     delete P;
     return kOK;
 }

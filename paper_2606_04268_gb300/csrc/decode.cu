@@ -458,6 +458,20 @@ cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, co
 
 }  // namespace aceapex
 
+namespace aceapex {
+__global__ void k_gather_status(int n, const int32_t *map, const int32_t *flat, const int32_t *wave, int32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t kind = map[2 * i], v = map[2 * i + 1];
+    out[i] = kind == 0 ? v : kind == 1 ? flat[v] : wave[v];
+}
+cudaError_t launch_gather_status(int n, const int32_t *map, const int32_t *flat, const int32_t *wave, int32_t *out,
+                                 cudaStream_t stream) {
+    k_gather_status<<<(n + 255) / 256, 256, 0, stream>>>(n, map, flat, wave, out);
+    return cudaGetLastError();
+}
+}  // namespace aceapex
+
 // Fresh persistent state of a served request (stream-ordered, no host memory involved).
 namespace aceapex {
 __global__ void k_state_init(StreamState *st) {

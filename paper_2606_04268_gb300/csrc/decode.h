@@ -51,6 +51,9 @@ int prof_collect(double *ms, unsigned long long *launches);  // kKCount entries 
 
 cudaError_t launch_flat(const LaunchCfg &cfg, WsHead *head, StreamState *sst, uint32_t *flags, const StreamDesc *descs,
                         const LaunchArgs &a, int32_t *status_out, cudaStream_t stream);
+// Batch plan statuses into device memory: out[i] = map (0, v): v; (1, k): flat[k]; (2, k): wave[k].
+cudaError_t launch_gather_status(int n, const int32_t *map, const int32_t *flat, const int32_t *wave, int32_t *out,
+                                 cudaStream_t stream);
 cudaError_t launch_wave(const LaunchCfg &cfg, WsHead *head, StreamState *sst, const LaunchArgs &a, const WaveBufs &wb,
                         int32_t *status_out, cudaStream_t stream);
 

@@ -244,6 +244,29 @@ def test_batch_reports_per_stream_errors():
     assert np.array_equal(outs[0].cpu().numpy(), xs[0]) and np.array_equal(outs[2].cpu().numpy(), xs[2])
 
 
+def test_batch_plan_device_statuses_match_host_statuses():
+    """The device-status form of a batch: one-pass, wavefront and malformed streams in one plan; the statuses
+    gathered on the device equal the host ones and the oracle's codes."""
+    xs = [synth.make("text", 30_000 + 7 * i, 50 + i) for i in range(5)]
+    comps = [oracle.encode(xs[0], flatten=2), oracle.encode(xs[1]), oracle.encode(xs[2], flatten=2),
+             oracle.encode(xs[3]), oracle.encode(xs[4], flatten=2)]
+    comps[2] = _mut(comps[2], 0, 4, 0)                       # bad magic: found on the host
+    b0 = int.from_bytes(bytes(comps[4][64:72]), "little")
+    comps[4] = _mut(comps[4], b0 + 32 + 20 + 4, 1, 77)        # a sync entry: found by the one-pass kernel
+    outs = [torch.zeros(x.size, dtype=torch.uint8, device="cuda") for x in xs]
+    plan = ax.BatchPlan([to_dev(c) for c in comps], outs)
+    try:
+        plan.launch()
+        d_st = torch.full((5,), 123, dtype=torch.int32, device="cuda")
+        plan.statuses_device(d_st)
+        host = plan.statuses()
+        assert np.array_equal(d_st.cpu().numpy(), host)
+        want = [oracle.decode_rc(c, x.size)[0] for c, x in zip(comps, xs)]
+        assert list(host) == want and want[2] != 0 and want[4] != 0 and want[0] == want[1] == want[3] == 0
+    finally:
+        plan.close()
+
+
 def test_bounded_wait_times_out_and_context_survives():
     """A tile whose flag is withheld makes every later tile's wait run out: the call returns
     ERR_TIMEOUT (no fault, no hang) and the next decode on the same context succeeds."""
