@@ -743,6 +743,7 @@ def run_batch(args):
     line["details"] = {"comp_bytes": C, "ratio": round(C / N, 4), "n_match": n_match,
                        "mean_match": round((N - n_lit) / max(n_match, 1), 2),
                        "autotuned": {"warps_per_cta": cfg[0], "ctas_per_sm": cfg[1]},
+                       "autotune_ms": {f"{k[0]} warps x {k[1] or 'max'} CTAs": round(v, 3) for k, v in times.items()},
                        "plain_one_at_a_time_gbs": round(N / (plain_ms * 1e-3) / 1e9, 3),
                        "batched_vs_plain": round(plain_ms / ms, 3), "encode_s": round(enc_s, 1)}
     line["decode_roofline_frac"] = round((C + 2 * N) / (ms * 1e-3) / 1e9 / hbm_peak, 4)
