@@ -505,6 +505,24 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     hbm_peak, peak_kind = peaks()
+    if args.transcode:
+        # the stream transcoded on the device into a flattened one, then that stream decoded
+        def barrier1():
+            torch.cuda.synchronize()
+        deep_ms = measure_stream(ax, torch, x, comp, args.steps, args.warmup, hbm_peak, peak_kind, args.workload,
+                                 barrier1, e2e=False)["ms"]
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            r = measure_transcode(ax, torch, x, comp, args.steps, args.warmup, hbm_peak, peak_kind, barrier1, deep_ms)
+        line = _base_line(args, x.size / (r["ms"] * 1e-3) / 1e9, r["ms"], desc + ", transcoded on the device",
+                          {k: v for k, v in single_config(args, world).items() if k != "workload"})
+        line["details"] = {k: r[k] for k in ("transcode_ms", "transcode_gbs", "ratio", "input_ratio",
+                                             "decodes_to_repay_transcode")}
+        line["details"]["decode_ms_before"] = round(deep_ms, 4)
+        for k in ("decode_roofline_frac", "roofline", "kernels_ms", "gpu_launches"):
+            line[k] = r[k]
+        line["clocks"] = clk.summary()
+        print(json.dumps(line), flush=True)
+        return
     if args.entropy:
         # the stream in the entropy container: a step is the GPU entropy decode plus the decode
         with ClockSampler(torch.cuda.current_device()) as clk:
@@ -856,7 +874,8 @@ def measure_transcode(ax, torch, x, comp, steps, warmup, hbm_peak, peak_kind, ba
     for _ in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        t = ax.transcode_flat(d_comp)  # synchronous: create (analysis) + write
+        with nvtx_range("transcode"):
+            t = ax.transcode_flat(d_comp)  # synchronous: create (analysis) + write
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     tc_ms = 1e3 * float(np.median(times))
@@ -1068,6 +1087,8 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="batch workload: skip the single-stream configurations measured beside it")
     ap.add_argument("--size", type=int, default=0, help="override the workload size (bytes)")
+    ap.add_argument("--transcode", action="store_true",
+                    help="single-stream workloads: transcode the stream on the device into a flattened one, then decode it")
     ap.add_argument("--entropy", action="store_true",
                     help="single-stream workloads: the stream in the entropy container (GPU entropy decode + decode)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
