@@ -79,11 +79,12 @@ __global__ void k_tc_root_init(uint32_t *root, uint64_t n4) {
 // Level k's matches are entries [lvl[k], lvl[k+1]) of the level-ordered records.  A warp takes 32 of them:
 // each lane copies the roots of its own match when it is at most 32 bytes long, the whole warp copies the
 // longer ones.  Roots of lower levels were written by other SMs before the grid barrier: loads go through L2.
-__global__ void __launch_bounds__(kTcNT) k_tc_roots(WsHead *head, StreamState *st, WaveBufs wb, uint32_t nlev,
-                                                    uint32_t *root, unsigned long long wait_ns) {
+constexpr int kTcRootNT = 256;  // up to 4 CTAs per SM (one 1024-thread CTA per SM measured slower)
+__global__ void __launch_bounds__(kTcRootNT) k_tc_roots(WsHead *head, StreamState *st, WaveBufs wb, uint32_t nlev,
+                                                        uint32_t *root, unsigned long long wait_ns) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (kTcNT / 32);
-    const uint64_t gw = (uint64_t)blockIdx.x * (kTcNT / 32) + (threadIdx.x >> 5);
+    const uint64_t warps = (uint64_t)gridDim.x * (kTcRootNT / 32);
+    const uint64_t gw = (uint64_t)blockIdx.x * (kTcRootNT / 32) + (threadIdx.x >> 5);
     const uint64_t t0 = global_ns();
     for (uint32_t k = 1; k <= nlev; k++) {
         const uint32_t a = wb.lvl[k], b = wb.lvl[k + 1];
@@ -330,12 +331,15 @@ __global__ void __launch_bounds__(kTcNT) k_tc_block_sizes(TcArgs a) {
 }
 
 // One block of the result (one CTA per block): header, sync table, sections.  The result buffer is zeroed
-// first (padding), so only the fields and sections are written.  Sequences are taken kTcNT at a time; their
-// section offsets come from block scans; literal runs are copied by a warp each, long ones by the CTA.
-constexpr uint32_t kTcLongRun = 512;
-__global__ void __launch_bounds__(kTcNT) k_tc_write(TcArgs a) {
-    __shared__ ScanSmem<kTcNT> sm;
-    __shared__ uint32_t s_src[kTcNT], s_dst[kTcNT], s_len[kTcNT];
+// first (padding), so only the fields and sections are written.  Sequences are taken kTcWNT at a time; their
+// section offsets come from CTA scans; a thread copies its own literal run when it is short, a warp each
+// medium one, the whole CTA each long one.
+constexpr int kTcWNT = 1024;
+constexpr uint32_t kTcShortRun = 32, kTcLongRun = 512;
+__global__ void __launch_bounds__(kTcWNT) k_tc_write(TcArgs a) {
+    __shared__ ScanSmem<kTcWNT> sm;
+    __shared__ uint32_t s_src[kTcWNT], s_dst[kTcWNT], s_len[kTcWNT], s_med[kTcWNT], s_long[kTcWNT];
+    __shared__ uint32_t s_nmed, s_nlong;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t *__restrict__ x = a.x;
     for (uint64_t b = blockIdx.x; b < a.n_blocks; b += gridDim.x) {
@@ -352,7 +356,8 @@ __global__ void __launch_bounds__(kTcNT) k_tc_write(TcArgs a) {
         const uint64_t o_lit = align16(o_off + (uint64_t)k.n_match * k.w);
         const uint32_t np = P1 - P0, tl = a.tile_log2, T = 1u << tl;
         unsigned long long cp = 0, lp = 0, lt = 0;
-        for (uint32_t i0 = 0; i0 < k.n_seq; i0 += kTcNT) {
+        for (uint32_t i0 = 0; i0 < k.n_seq; i0 += kTcWNT) {
+            if (threadIdx.x == 0) { s_nmed = 0; s_nlong = 0; }  // ordered by the scans' barriers below
             const uint32_t i = i0 + threadIdx.x;
             const bool valid = i < k.n_seq, has = i < np;
             uint32_t pos = 0, r = 0, L = 0, s = 0;
@@ -364,9 +369,9 @@ __global__ void __launch_bounds__(kTcNT) k_tc_write(TcArgs a) {
             }
             const uint32_t vr = valid ? vlen(r) : 0u, vl = has ? vlen(L - a.min_match) : 0u;
             unsigned long long tc, tlp, tlt;
-            const unsigned long long ec = cp + block_excl_scan<kTcNT>(vr, sm, tc);
-            const unsigned long long el = lp + block_excl_scan<kTcNT>(vl, sm, tlp);
-            const unsigned long long et = lt + block_excl_scan<kTcNT>(valid ? r : 0u, sm, tlt);
+            const unsigned long long ec = cp + block_excl_scan<kTcWNT>(vr, sm, tc);
+            const unsigned long long el = lp + block_excl_scan<kTcWNT>(vl, sm, tlp);
+            const unsigned long long et = lt + block_excl_scan<kTcWNT>(valid ? r : 0u, sm, tlt);
             if (valid) {
                 put_varint(h + o_cmd + ec, r);
                 if (has) {
@@ -380,30 +385,38 @@ __global__ void __launch_bounds__(kTcNT) k_tc_write(TcArgs a) {
                     put32(e, i); put32(e + 4, (uint32_t)ec); put32(e + 8, (uint32_t)el); put32(e + 12, (uint32_t)et);
                     put32(e + 16, rel);
                 }
+                if (r <= kTcShortRun) {
+                    const uint8_t *src = x + pos;
+                    uint8_t *dst = h + o_lit + et;
+                    for (uint32_t q = 0; q < r; q++) dst[q] = __ldg(src + q);
+                } else if (r < kTcLongRun) {
+                    s_med[atomicAdd(&s_nmed, 1u)] = threadIdx.x;
+                } else {
+                    s_long[atomicAdd(&s_nlong, 1u)] = threadIdx.x;
+                }
             }
             s_src[threadIdx.x] = pos;
             s_dst[threadIdx.x] = (uint32_t)et;
             s_len[threadIdx.x] = valid ? r : 0u;
             __syncthreads();
-            for (uint32_t q = warp; q < kTcNT; q += kTcNT / 32) {
-                const uint32_t n = s_len[q];
-                if (n >= kTcLongRun) continue;
-                const uint8_t *src = x + s_src[q];
-                uint8_t *dst = h + o_lit + s_dst[q];
+            const uint32_t nmed = s_nmed, nlong = s_nlong;
+            for (uint32_t q = warp; q < nmed; q += kTcWNT / 32) {
+                const uint32_t t = s_med[q], n = s_len[t];
+                const uint8_t *src = x + s_src[t];
+                uint8_t *dst = h + o_lit + s_dst[t];
                 for (uint32_t j = lane; j < n; j += 32) dst[j] = __ldg(src + j);
             }
-            for (uint32_t q = 0; q < kTcNT; q++) {
-                const uint32_t n = s_len[q];
-                if (n < kTcLongRun) continue;
-                const uint8_t *src = x + s_src[q];
-                uint8_t *dst = h + o_lit + s_dst[q];
+            for (uint32_t q = 0; q < nlong; q++) {
+                const uint32_t t = s_long[q], n = s_len[t];
+                const uint8_t *src = x + s_src[t];
+                uint8_t *dst = h + o_lit + s_dst[t];
                 uint32_t j = threadIdx.x;
-                for (; j + 3 * kTcNT < n; j += 4 * kTcNT) {
-                    const uint8_t v0 = __ldg(src + j), v1 = __ldg(src + j + kTcNT), v2 = __ldg(src + j + 2 * kTcNT),
-                                  v3 = __ldg(src + j + 3 * kTcNT);
-                    dst[j] = v0; dst[j + kTcNT] = v1; dst[j + 2 * kTcNT] = v2; dst[j + 3 * kTcNT] = v3;
+                for (; j + 3 * kTcWNT < n; j += 4 * kTcWNT) {
+                    const uint8_t v0 = __ldg(src + j), v1 = __ldg(src + j + kTcWNT), v2 = __ldg(src + j + 2 * kTcWNT),
+                                  v3 = __ldg(src + j + 3 * kTcWNT);
+                    dst[j] = v0; dst[j + kTcWNT] = v1; dst[j + 2 * kTcWNT] = v2; dst[j + 3 * kTcWNT] = v3;
                 }
-                for (; j < n; j += kTcNT) dst[j] = __ldg(src + j);
+                for (; j < n; j += kTcWNT) dst[j] = __ldg(src + j);
             }
             __syncthreads();
             cp += tc; lp += tlp; lt += tlt;
@@ -488,12 +501,13 @@ int tc_build(aceapex_transcode *t, const void *comp, cudaStream_t stream) {
         WsHead *head = (WsHead *)t->aux;
         StreamState *st = (StreamState *)(t->aux + 256);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tc_roots, kTcNT, 0);
-        const unsigned grid = (unsigned)std::max(1, std::min(occ, 4)) * (unsigned)t->num_sms;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tc_roots, kTcRootNT, 0);
+        if (occ < 1) return kErrCuda;
+        const unsigned grid = (unsigned)std::min(occ, 4) * (unsigned)t->num_sms;
         uint32_t nlev = I.max_depth;
         unsigned long long wait_ns = 4000000000ull;
         void *args[] = {(void *)&head, (void *)&st, (void *)&t->wb, (void *)&nlev, (void *)&t->root, (void *)&wait_ns};
-        if ((rc = tc_fail(cudaLaunchCooperativeKernel((void *)k_tc_roots, grid, kTcNT, args, 0, stream)))) return rc;
+        if ((rc = tc_fail(cudaLaunchCooperativeKernel((void *)k_tc_roots, grid, kTcRootNT, args, 0, stream)))) return rc;
         int32_t hst = 0;
         cudaError_t e = cudaMemcpyAsync(&hst, &st->status, 4, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -604,7 +618,7 @@ int aceapex_transcode_write(aceapex_transcode *t, void *out, size_t out_cap, voi
         a.base = t->base; a.pd = t->pd; a.ps = t->ps; a.pl = t->pl; a.x = t->x;
         a.N = I.decoded_len; a.n_blocks = I.n_blocks; a.block_log2 = I.block_log2; a.tile_log2 = I.tile_log2;
         a.min_match = I.min_match; a.blk = t->blk; a.boff = t->boff; a.out = (uint8_t *)out;
-        k_tc_write<<<(unsigned)std::min<uint64_t>(I.n_blocks, 65535), kTcNT, 0, stream>>>(a);
+        k_tc_write<<<(unsigned)std::min<uint64_t>(I.n_blocks, 65535), kTcWNT, 0, stream>>>(a);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return tc_fail(e);
