@@ -220,7 +220,8 @@ bool use_wave(const aceapex_info &I) { return !one_pass_fits(I) || ctx().force_w
 // Enqueue the decode of one stream into workspace ws (layout L); the status goes to status_out.
 // wave_sched >= 0 overrides the scheduler of the wavefront path.
 int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, const WsLayout &L,
-                int32_t *status_out, int num_sms, cudaStream_t stream, int wave_sched = -1) {
+                int32_t *status_out, int num_sms, cudaStream_t stream, int wave_sched = -1,
+                uint32_t *root = nullptr) {
     LaunchCfg cfg = ctx().cfg;
     cfg.num_sms = num_sms;
     if (wave_sched >= 0) cfg.wave_sched = wave_sched;
@@ -235,6 +236,7 @@ int enqueue_one(const void *comp, void *out, const aceapex_info &I, uint8_t *ws,
     a.max_n = I.decoded_len;
     WsHead *head = (WsHead *)(ws + L.head);
     a.phase = prof_enabled() ? head->phase : nullptr;
+    a.root = root;
     StreamState *sst = (StreamState *)(ws + L.sst);
     cudaError_t e;
     if (use_wave(I) || wave_sched >= 0) e = launch_wave(cfg, head, sst, a, wave_bufs(ws, L), status_out, stream);
@@ -286,12 +288,13 @@ int server_enqueue_whole(const void *comp, void *out, const aceapex_info &I, uin
     return enqueue_one(comp, out, I, *ws, L, status_out ? status_out : (int32_t *)(*ws + L.status), p->num_sms, stream);
 }
 
-// Transcoder (transcode.cu): header parsing, and a decode by the wavefront path with level queues that leaves
-// every match's record (stream order and level order) and the level offsets in the caller's workspace.
+// Transcoder (transcode.cu): header parsing, and a decode by the wavefront path's warp dataflow that leaves
+// every match's record (stream order) in the caller's workspace and copies every byte's root with the byte
+// (root[] holds y at every position beforehand).
 int tc_parse_header(const uint8_t *h, size_t len, aceapex_info *info) { return parse_header(h, len, info); }
 size_t tc_workspace_size(const aceapex_info &I) { return layout_one(I, true).total; }
-int tc_decode(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, WaveBufs *wb, int32_t *status,
-              int *num_sms, cudaStream_t stream) {
+int tc_decode(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, WaveBufs *wb, uint32_t *root,
+              int32_t *status, int *num_sms, cudaStream_t stream) {
     std::lock_guard<std::mutex> g(ctx().mu);
     DevPool *p = nullptr;
     int rc = pool_for_device(&p);
@@ -300,7 +303,7 @@ int tc_decode(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, W
     if (cudaMemsetAsync(ws, 0, L.total, stream) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
     *wb = wave_bufs(ws, L);
     *num_sms = p->num_sms;
-    return enqueue_one(comp, out, I, ws, L, status, p->num_sms, stream, 1);
+    return enqueue_one(comp, out, I, ws, L, status, p->num_sms, stream, 2, root);
 }
 }  // namespace aceapex_host
 

@@ -17,6 +17,7 @@ struct LaunchArgs {
     unsigned int max_tile_log2;   // largest tile of the launch's streams (selects the image kernel)
     unsigned long long max_n;     // largest decoded length of the launch's streams (0 = unknown)
     unsigned long long *phase;    // when profiling: per-phase SM cycles of the one-pass kernel (kPhases)
+    uint32_t *root;               // transcoding (warp dataflow only): per output byte, its root, copied with it
 };
 constexpr int kPhases = 8;  // open, parse, literals, store+publish, wait, matches, store, tiles
 

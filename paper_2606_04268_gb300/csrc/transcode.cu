@@ -1,5 +1,5 @@
 // Transcoding a stream into a globally chain-flattened stream, on the GPU (chain flattening of §3.3 applied
-// to an existing stream; the levels of §7.1 order the root computation).  Every match byte has a root, the
+// to an existing stream; the match dependencies of §7.1 order the root computation).  Every match byte has a root, the
 // literal byte it ultimately copies: a literal byte is its own root, and byte k of a match with destination
 // d, source s and period p = d - s has the root of byte s + (k mod p).  Each match becomes
 //   - itself, when it overlaps itself (p < L) and its effective source [s, d) is literal;
@@ -11,11 +11,11 @@
 // tile size and min_match, and has flatten mode 2 and no depth cap.
 //
 // Device steps:
-//   1. decode by the wavefront path with level queues (api.cpp): the decoded bytes, each match's record in
-//      stream order and in level order, the level offsets;
-//   2. k_tc_root_init, k_tc_roots: root[y] = y, then level after level in one cooperative launch (bounded grid
-//      barrier between levels) root[d + k] = root[s + (k mod p)] -- a level's sources are literal bytes or
-//      bytes of lower levels, whose roots are final;
+//   1. k_tc_root_init: root[y] = y for every output byte;
+//   2. the decode by the wavefront path's warp dataflow (api.cpp, k_flow_w): every match is copied once the
+//      matches that wrote its source bytes are done, and its bytes' roots with it, root[d + k] =
+//      root[s + (k mod p)] (§7.1 orders the work without level barriers); each match's record stays in the
+//      workspace in stream order;
 //   3. k_tc_pieces<false> counts the matches each match becomes, k_tc_scan_* turn the counts into offsets,
 //      k_tc_pieces<true> writes them (destination, source, length) in destination order;
 //   4. k_tc_block_sizes: per block its sequence count, section sizes, offset width and size; the host lays
@@ -23,7 +23,6 @@
 //   5. k_tc_write: per block the block header, the sync table, the cmd/len varints, the offsets and the
 //      literal bytes.
 // Positions are 32-bit: streams of up to 2^32 - 1 decoded bytes.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -40,8 +39,8 @@ using namespace aceapex;
 namespace aceapex_host {
 int tc_parse_header(const uint8_t *h, size_t len, aceapex_info *info);
 size_t tc_workspace_size(const aceapex_info &I);
-int tc_decode(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, WaveBufs *wb, int32_t *status,
-              int *num_sms, cudaStream_t stream);
+int tc_decode(const void *comp, void *out, const aceapex_info &I, uint8_t *ws, WaveBufs *wb, uint32_t *root,
+              int32_t *status, int *num_sms, cudaStream_t stream);
 }  // namespace aceapex_host
 
 namespace aceapex {
@@ -73,43 +72,6 @@ __global__ void k_tc_root_init(uint32_t *root, uint64_t n4) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t y = (uint32_t)(4 * i);
         reinterpret_cast<uint4 *>(root)[i] = make_uint4(y, y + 1, y + 2, y + 3);
-    }
-}
-
-// Level k's matches are entries [lvl[k], lvl[k+1]) of the level-ordered records.  A warp takes 32 of them:
-// each lane copies the roots of its own match when it is at most 32 bytes long, the whole warp copies the
-// longer ones.  Roots of lower levels were written by other SMs before the grid barrier: loads go through L2.
-constexpr int kTcRootNT = 256;  // up to 4 CTAs per SM (one 1024-thread CTA per SM measured slower)
-__global__ void __launch_bounds__(kTcRootNT) k_tc_roots(WsHead *head, StreamState *st, WaveBufs wb, uint32_t nlev,
-                                                        uint32_t *root, unsigned long long wait_ns) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (kTcRootNT / 32);
-    const uint64_t gw = (uint64_t)blockIdx.x * (kTcRootNT / 32) + (threadIdx.x >> 5);
-    const uint64_t t0 = global_ns();
-    for (uint32_t k = 1; k <= nlev; k++) {
-        const uint32_t a = wb.lvl[k], b = wb.lvl[k + 1];
-        for (uint64_t g = a + 32 * gw; g < b; g += 32 * warps) {
-            const uint64_t m = g + lane;
-            uint32_t d = 0, s = 0, L = 0;
-            if (m < b) { d = (uint32_t)wb.qd[m]; s = (uint32_t)wb.qs[m]; L = wb.ql[m]; }
-            const uint32_t p = d - s;
-            if (L <= 32) {
-                uint32_t q = 0;
-                for (uint32_t j = 0; j < L; j++) {
-                    root[d + j] = __ldcg(root + s + q);
-                    if (++q == p) q = 0;
-                }
-            }
-            unsigned longs = __ballot_sync(0xffffffffu, L > 32);
-            while (longs) {
-                const int o = __ffs(longs) - 1;
-                longs &= longs - 1;
-                const uint32_t od = __shfl_sync(0xffffffffu, d, o), os = __shfl_sync(0xffffffffu, s, o);
-                const uint32_t oL = __shfl_sync(0xffffffffu, L, o), op = od - os;
-                for (uint32_t j = lane; j < oL; j += 32) root[od + j] = __ldcg(root + os + (op >= oL ? j : j % op));
-            }
-        }
-        if (k < nlev && !grid_barrier(head, st, t0, wait_ns)) return;
     }
 }
 
@@ -433,7 +395,6 @@ struct aceapex_transcode {
     uint32_t *root = nullptr;
     uint8_t *ws = nullptr;       // wavefront workspace (records, level queues)
     WaveBufs wb{};
-    uint8_t *aux = nullptr;      // head + state of the root launch
     uint32_t *cnt = nullptr, *base = nullptr;
     unsigned long long *part = nullptr;
     uint32_t *pd = nullptr, *ps = nullptr, *pl = nullptr;
@@ -456,7 +417,7 @@ int tc_fail(cudaError_t e) {
 
 void tc_free(aceapex_transcode *t) {
     if (!t) return;
-    cudaFree(t->x); cudaFree(t->root); cudaFree(t->ws); cudaFree(t->aux); cudaFree(t->cnt); cudaFree(t->base);
+    cudaFree(t->x); cudaFree(t->root); cudaFree(t->ws); cudaFree(t->cnt); cudaFree(t->base);
     cudaFree(t->part); cudaFree(t->pd); cudaFree(t->ps); cudaFree(t->pl); cudaFree(t->blk); cudaFree(t->boff);
     cudaFree(t->zero_bb); cudaFree(t->d_status);
     delete t;
@@ -485,34 +446,24 @@ int tc_build(aceapex_transcode *t, const void *comp, cudaStream_t stream) {
     int rc;
     if ((rc = tc_alloc(&t->d_status, 1)) || (rc = tc_fail(cudaMemsetAsync(t->d_status, 0, 4, stream)))) return rc;
     if (N > 0) {
-        // 1. decode, with every match's record in stream order and in level order
-        if ((rc = tc_alloc(&t->x, N)) || (rc = tc_alloc(&t->ws, aceapex_host::tc_workspace_size(I)))) return rc;
-        if ((rc = aceapex_host::tc_decode(comp, t->x, I, t->ws, &t->wb, t->d_status, &t->num_sms, stream))) return rc;
+        // 1-2. roots start as root[y] = y; the decode by the warp dataflow copies every match byte's root with
+        // the byte (a match is copied once the matches that wrote its source are done, so the roots it reads
+        // are final) and leaves every match's record in stream order
+        const uint64_t n4 = (N + 3) / 4;
+        if ((rc = tc_alloc(&t->x, N)) || (rc = tc_alloc(&t->ws, aceapex_host::tc_workspace_size(I))) ||
+            (rc = tc_alloc(&t->root, 4 * n4)))
+            return rc;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k_tc_root_init<<<(unsigned)std::min<uint64_t>((n4 + kTcNT - 1) / kTcNT, (uint64_t)sms * 16), kTcNT, 0,
+                         stream>>>(t->root, n4);
+        if ((rc = tc_fail(cudaGetLastError()))) return rc;
+        if ((rc = aceapex_host::tc_decode(comp, t->x, I, t->ws, &t->wb, t->root, t->d_status, &t->num_sms, stream)))
+            return rc;
         if ((rc = tc_status(t, stream))) return rc;
     }
     if (nm > 0) {
-        // 2. roots
-        const uint64_t n4 = (N + 3) / 4;
-        if ((rc = tc_alloc(&t->root, 4 * n4))) return rc;
-        const size_t aux = 256 + sizeof(StreamState);
-        if ((rc = tc_alloc(&t->aux, aux)) || (rc = tc_fail(cudaMemsetAsync(t->aux, 0, aux, stream)))) return rc;
-        k_tc_root_init<<<(unsigned)std::min<uint64_t>((n4 + kTcNT - 1) / kTcNT, (uint64_t)t->num_sms * 16), kTcNT, 0,
-                         stream>>>(t->root, n4);
-        WsHead *head = (WsHead *)t->aux;
-        StreamState *st = (StreamState *)(t->aux + 256);
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tc_roots, kTcRootNT, 0);
-        if (occ < 1) return kErrCuda;
-        const unsigned grid = (unsigned)std::min(occ, 4) * (unsigned)t->num_sms;
-        uint32_t nlev = I.max_depth;
-        unsigned long long wait_ns = 4000000000ull;
-        void *args[] = {(void *)&head, (void *)&st, (void *)&t->wb, (void *)&nlev, (void *)&t->root, (void *)&wait_ns};
-        if ((rc = tc_fail(cudaLaunchCooperativeKernel((void *)k_tc_roots, grid, kTcRootNT, args, 0, stream)))) return rc;
-        int32_t hst = 0;
-        cudaError_t e = cudaMemcpyAsync(&hst, &st->status, 4, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) return tc_fail(e);
-        if (hst) return hst;
         // 3. the matches each match becomes
         const uint64_t per = (uint64_t)kTcNT * kTcItems, nparts = (nm + per - 1) / per;
         if ((rc = tc_alloc(&t->cnt, nm)) || (rc = tc_alloc(&t->base, nm + 1)) || (rc = tc_alloc(&t->part, nparts)))
@@ -524,7 +475,7 @@ int tc_build(aceapex_transcode *t, const void *comp, cudaStream_t stream) {
         k_tc_scan_top<<<1, kTcNT, 0, stream>>>(t->part, nparts, t->base, nm);
         k_tc_scan_down<<<(unsigned)nparts, kTcNT, 0, stream>>>(t->cnt, nm, t->part, t->base);
         uint32_t total = 0;
-        e = cudaMemcpyAsync(&total, t->base + nm, 4, cudaMemcpyDeviceToHost, stream);
+        cudaError_t e = cudaMemcpyAsync(&total, t->base + nm, 4, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return tc_fail(e);
         t->n_out_match = total;

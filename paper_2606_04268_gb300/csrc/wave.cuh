@@ -326,11 +326,19 @@ __global__ void __launch_bounds__(32 * kFlowWarps, 8) k_flow_w(WsHead *head, Str
                             if (++km == (uint32_t)p) km = 0;
                         }
                     }
+                    if (a.root) {
+                        // transcoding: every byte's root travels with it, root[d+k] = root[s + (k mod p)]
+                        uint64_t km = 0;
+                        for (uint64_t k = 0; k < L; k++) {
+                            a.root[d + k] = __ldcg(a.root + s + km);
+                            if (++km == p) km = 0;
+                        }
+                    }
                     uint32_t dep = mx + 1;
                     // a match deeper than its block's max_depth field: the stream understates its depth
                     if (L && dep > wb.bdepth[d >> sd.block_log2]) report_depth(&sst[0]);
                     if (dep > cap) dep = cap;
-                    st_release_u32(&wb.depth[m], dep);  // the bytes above are visible before the depth
+                    st_release_u32(&wb.depth[m], dep);  // the bytes (and roots) above are visible before the depth
                     mydep[sub] = dep;
                     dmax = dep > dmax ? dep : dmax;
                     done = true;
