@@ -738,13 +738,15 @@ def run_batch(args):
         h_comp = torch.empty(C, dtype=torch.uint8).pin_memory()
         h_comp.copy_(d_comp)
         h_out = torch.empty(N, dtype=torch.uint8).pin_memory()
-        barrier()
-        t1 = time.perf_counter()
-        d_comp.copy_(h_comp, non_blocking=True)
-        plan.launch(graph=True, stream=stream)
-        h_out.copy_(d_out, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t1
+        e2e_s = 0.0
+        for rep in range(2):  # the first pass is a warm-up (first use of the pinned buffers), the second is timed
+            barrier()
+            t1 = time.perf_counter()
+            d_comp.copy_(h_comp, non_blocking=True)
+            plan.launch(graph=True, stream=stream)
+            h_out.copy_(d_out, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t1
         assert (plan.statuses(stream) == 0).all()
     plan.close()
     ms = max_over_ranks(ms, world, "cuda")
