@@ -226,22 +226,29 @@ __device__ __forceinline__ uint32_t f4_owner(uint32_t ex, uint32_t i) {
     return k;
 }
 
+// Rarely taken paths are kept out of line (not inlined at each call site), which keeps the kernel's hot loop
+// small in the instruction cache: literals read from global memory (a section larger than the stage) and the
+// period-split copy of a self-overlapping match.
+__device__ __noinline__ void or_piece_lit_glob(uint32_t *imgw, uint32_t ib, const uint8_t *base, uint32_t off,
+                                              uint32_t len) {
+    or_piece_glob<true>(imgw, ib, base, off, len);
+}
+// Byte k of a self-overlapping match reads s + (k mod p): the piece is split at the period boundaries.
+__device__ __noinline__ void f4_match_wrap(uint32_t *imgw, uint32_t ib, const uint8_t *out, uint32_t s, uint32_t p,
+                                           uint32_t k, uint32_t len) {
+    uint32_t r = k % p;
+    while (len) {
+        const uint32_t c = (p - r) < len ? p - r : len;
+        or_piece_glob<false>(imgw, ib, out, s + r, c);
+        ib += c; len -= c;
+        r += c; if (r == p) r = 0;
+    }
+}
 // Match bytes [k, k + len) of a match with source s and period p (p >= length: no wrap) into the image.
 __device__ __forceinline__ void f4_match_piece(uint32_t *imgw, uint32_t ib, const uint8_t *out, uint32_t s,
                                                uint32_t p, uint32_t k, uint32_t len, bool wrap) {
-    if (!wrap) {
-        or_piece_glob<false>(imgw, ib, out, s + k, len);
-        return;
-    }
-    // byte k reads s + (k mod p): split at the period boundaries
-    const uint32_t pp = p;
-    uint32_t r = k % pp;
-    while (len) {
-        const uint32_t c = (pp - r) < len ? pp - r : len;
-        or_piece_glob<false>(imgw, ib, out, s + r, c);
-        ib += c; len -= c;
-        r += c; if (r == pp) r = 0;
-    }
+    if (!wrap) or_piece_glob<false>(imgw, ib, out, s + k, len);
+    else f4_match_wrap(imgw, ib, out, s, p, k, len);
 }
 
 // ------------------------------------------------------------------------------------------ literal bits
@@ -266,6 +273,24 @@ __device__ __forceinline__ bool f4_bits(const uint32_t *w, uint32_t a, uint32_t 
         ok = (v & m) == m;
     }
     return ok;
+}
+
+// The slow part of a match's wait for its source tiles, out of line (most matches find their sources
+// published at the first look): poll the flags of stream tiles [need, need_hi] (flag of tile u at fl[u - toff])
+// every 64 ns until all lanes' tiles are published, or until wait_ns has passed (kErrTimeout).
+__device__ __noinline__ int f4_wait_slow(const uint32_t *fl, uint32_t toff, uint32_t need, uint32_t need_hi,
+                                         uint32_t epoch, unsigned long long wait_ns) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        __nanosleep(64);
+        bool ok = true;
+        while (need <= need_hi) {
+            if (ld_acquire_u32(&fl[need - toff]) != epoch) { ok = false; break; }
+            need++;
+        }
+        if (__all_sync(kFull, ok)) return 0;
+        if (__any_sync(kFull, global_ns() - t0 > wait_ns)) return kErrTimeout;
+    }
 }
 
 // ------------------------------------------------------------------------------------------ kernel
@@ -437,14 +462,14 @@ __global__ void __launch_bounds__(32 * WARPS, 20 / WARPS) k_flat(WsHead *head, S
                     const uint32_t first = len < 16 ? len : 16u;
                     if (first) {
                         if (smem_src) or_piece_smem(wbase, imgw, ib, so, first);
-                        else or_piece_glob<true>(imgw, ib, c.lit, src, first);
+                        else or_piece_lit_glob(imgw, ib, c.lit, src, first);
                         f4_mark(W.lbm, ib, first);
                     }
                     if (__any_sync(kFull, len > 16)) {
                         const uint32_t second = len > 32 ? 16u : (len > 16 ? len - 16 : 0u);
                         if (second) {
                             if (smem_src) or_piece_smem(wbase, imgw, ib + 16, so + 16, second);
-                            else or_piece_glob<true>(imgw, ib + 16, c.lit, src + 16, second);
+                            else or_piece_lit_glob(imgw, ib + 16, c.lit, src + 16, second);
                             f4_mark(W.lbm, ib + 16, second);
                         }
                     }
@@ -469,7 +494,7 @@ __global__ void __launch_bounds__(32 * WARPS, 20 / WARPS) k_flat(WsHead *head, S
                                 const uint32_t off = 16 * (2 + i - o_ex);
                                 const uint32_t pl = (o_len - off) < 16 ? o_len - off : 16u;
                                 if (smem_src) or_piece_smem(wbase, imgw, o_ib + off, o_so + off, pl);
-                                else or_piece_glob<true>(imgw, o_ib + off, c.lit, o_src + off, pl);
+                                else or_piece_lit_glob(imgw, o_ib + off, c.lit, o_src + off, pl);
                                 f4_mark(W.lbm, o_ib + off, pl);
                             }
                         }
@@ -528,17 +553,13 @@ __global__ void __launch_bounds__(32 * WARPS, 20 / WARPS) k_flat(WsHead *head, S
                                 need_hi = ub < ord32 ? ub : ord32 - 1;
                             }
                         }
-                        const uint64_t t0 = global_ns();
-                        for (;;) {
-                            bool ok = true;
-                            while (need <= need_hi) {
-                                if (ld_acquire_u32(&flags[need - toff + (uint32_t)sd.tile_base]) != epoch) { ok = false; break; }
-                                need++;
-                            }
-                            if (__all_sync(kFull, ok)) break;
-                            if (__any_sync(kFull, global_ns() - t0 > a.wait_ns)) { err = kErrTimeout; break; }
-                            __nanosleep(64);
+                        bool ok = true;
+                        const uint32_t *fl = flags + sd.tile_base;  // fl[u - toff]: flag of stream tile u
+                        while (need <= need_hi) {
+                            if (ld_acquire_u32(&fl[need - toff]) != epoch) { ok = false; break; }
+                            need++;
                         }
+                        if (!__all_sync(kFull, ok)) err = f4_wait_slow(fl, toff, need, need_hi, epoch, a.wait_ns);
                         err = __shfl_sync(kFull, err, 0);
                         if (err) { if (lane == 0) report(st, kErrTimeout, kOrderTimeout); break; }
                         __syncwarp();
