@@ -147,6 +147,26 @@ int aceapex_decode_batch(int n, const void *const *comps, const size_t *comp_len
                          const size_t *out_lens, int32_t *statuses, void *stream);
 
 /*
+ * Decode n independent streams held in HOST memory into host buffers (blocking; §7.5 batching of
+ * independent streams, each decoded as in aceapex_decode, §3.1-§3.2 and §7.1).  h_comps/h_outs: host
+ * arrays of n host pointers (any alignment; pinned memory lets the copies run asynchronously, pageable
+ * memory works but serialises); comp_lens/out_lens: host arrays; statuses: host array of n int32 that
+ * receives each stream's status (ACEAPEX_ERR_ARG for a null pointer or a stream shorter than its header,
+ * ACEAPEX_ERR_SIZE when the lengths disagree with the header, else the decode status).
+ * The streams are cut into about 32 groups of consecutive streams.  A group's stream bytes are copied to
+ * device memory that the library owns (kept for later calls, grown on demand), its streams are decoded
+ * together (one persistent one-pass launch; deeper streams one after another) and its outputs are copied
+ * back, on three CUDA streams, so both copy directions overlap the decodes of other groups.  Streams whose
+ * host bytes follow each other share one copy: copies in also carry host gaps of up to 64 KiB between
+ * streams (read only), copies out join only outputs that are back to back, so no byte outside the outputs
+ * is written.  Host buffers are only read / written during the call; work is ordered after the caller's
+ * earlier work on `stream`.  Returns 0 when every stream decoded, else the first failing status in stream
+ * order; ACEAPEX_ERR_NOMEM when the device or pinned buffers cannot be allocated.
+ */
+int aceapex_decode_batch_host(int n, const void *const *h_comps, const size_t *comp_lens, void *const *h_outs,
+                              const size_t *out_lens, int32_t *statuses, void *stream);
+
+/*
  * Reusable batch plan (for repeated decodes of the same set of buffers): reads the headers once, builds the
  * device descriptor table and workspace.  plan_launch enqueues the decode; with graph != 0 the launch
  * sequence is captured into a CUDA graph on first use and replayed afterwards.  plan_statuses copies the

@@ -121,7 +121,7 @@ SYMBOLS = ["aceapex_peek_header", "aceapex_workspace_size", "aceapex_decode", "a
            "aceapex_decode_noalloc",
            "aceapex_decode_batch", "aceapex_batch_plan_create", "aceapex_batch_plan_launch",
            "aceapex_batch_plan_statuses", "aceapex_batch_plan_statuses_device", "aceapex_batch_plan_destroy", "aceapex_set_launch_config",
-           "aceapex_decode_host", "aceapex_get_launch_config", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
+           "aceapex_decode_host", "aceapex_decode_batch_host", "aceapex_get_launch_config", "aceapex_set_wave_scheduler", "aceapex_set_force_wavefront", "aceapex_set_wait_limit", "aceapex_profile",
            "aceapex_profile_read", "aceapex_get_stats", "aceapex_strerror",
            "aceapex_server_create", "aceapex_server_submit", "aceapex_server_step", "aceapex_server_poll",
            "aceapex_server_release", "aceapex_server_destroy",
@@ -158,6 +158,7 @@ def lib():
             L.aceapex_get_launch_config.argtypes = [ctypes.POINTER(ctypes.c_int)] * 2
             L.aceapex_set_force_wavefront.argtypes = [i32]
             L.aceapex_decode_host.argtypes = [p, sz, p, sz, p]
+            L.aceapex_decode_batch_host.argtypes = [i32, p, p, p, p, p, p]
             L.aceapex_set_wave_scheduler.argtypes = [i32]
             L.aceapex_set_wait_limit.argtypes = [u64, u64]
             L.aceapex_profile.argtypes = [i32]
@@ -294,6 +295,41 @@ def decode_batch(comps, outs, stream=None) -> np.ndarray:
     st = np.zeros(max(n, 1), np.int32)
     lib().aceapex_decode_batch(n, cp, cl, op, ol, st.ctypes.data, _stream_ptr(stream))
     return st[:n]
+
+
+class HostBatch:
+    """Pointer and length arrays of n host-memory streams and their host outputs, for decode_batch_host.
+    comps/outs: uint8 numpy arrays or CPU tensors (pinned memory lets the copies overlap the decodes).
+    Built once, the arrays serve every later call on the same buffers."""
+
+    def __init__(self, comps, outs):
+        assert len(comps) == len(outs)
+        self._keep = (list(comps), list(outs))
+        n = len(comps)
+        c = [_host_ptr(x) for x in comps]
+        o = [_host_ptr(x) for x in outs]
+        self.n = n
+        self.cp = (ctypes.c_void_p * max(n, 1))(*[a for a, _ in c])
+        self.cl = (ctypes.c_size_t * max(n, 1))(*[b for _, b in c])
+        self.op = (ctypes.c_void_p * max(n, 1))(*[a if b else None for a, b in o])
+        self.ol = (ctypes.c_size_t * max(n, 1))(*[b for _, b in o])
+        self.statuses = np.zeros(max(n, 1), np.int32)
+
+
+def decode_batch_host_status(batch: "HostBatch", stream=None) -> int:
+    """Decode the streams of a HostBatch from host memory into its host outputs (aceapex_decode_batch_host:
+    copies in, decodes and copies out overlapped).  Returns the first failing status (0: all decoded); the
+    per-stream statuses are in batch.statuses[:batch.n]."""
+    return lib().aceapex_decode_batch_host(batch.n, batch.cp, batch.cl, batch.op, batch.ol,
+                                           batch.statuses.ctypes.data, _stream_ptr(stream))
+
+
+def decode_batch_host(comps, outs, stream=None) -> np.ndarray:
+    """Decode many streams held in host memory into host buffers (blocking); returns the per-stream
+    status codes."""
+    b = HostBatch(comps, outs)
+    decode_batch_host_status(b, stream)
+    return b.statuses[:b.n].copy()
 
 
 class BatchPlan:

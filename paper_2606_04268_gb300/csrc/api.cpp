@@ -159,6 +159,10 @@ struct DevPool {
     StreamState *hd_state = nullptr;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev_in[kHostSlices]{}, ev_dec[kHostSlices]{};
+    // host-buffer batch decodes: device copies of the streams and outputs, the groups' workspaces, and pinned
+    // staging of the descriptors and statuses
+    uint8_t *hb_comp = nullptr, *hb_out = nullptr, *hb_ws = nullptr, *hb_pin = nullptr;
+    size_t hb_comp_cap = 0, hb_out_cap = 0, hb_ws_cap = 0, hb_pin_cap = 0;
 };
 
 struct Context {
@@ -801,6 +805,238 @@ int aceapex_decode_host(const void *h_comp, size_t comp_len, void *h_out, size_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e);
     return *h_status;
+}
+
+// ------------------------------------------------------------------------------------------ batch, host buffers
+namespace {
+constexpr uint64_t kBatchHostGap = 64 * 1024;  // a host gap up to this size between streams is copied in too
+constexpr int kBatchHostGroups = 32;           // about this many copy-in / decode / copy-out groups per call
+
+struct HostRun {  // one copy of len bytes between host memory and device offset dev
+    uint64_t dev;
+    uint8_t *host;
+    uint64_t len;
+};
+struct HostGroup {
+    std::vector<int> flat, wave;    // the group's streams by path, in stream order
+    std::vector<uint64_t> lm_at;    // per one-pass stream: word offset of its literal bitmap
+    std::vector<HostRun> in, out;   // copies in and out
+    WsLayout L{};                   // one-pass workspace, at ws_at in the batch workspace
+    uint64_t ws_at = 0, tiles = 0, lm_words = 0;
+    uint64_t pin_desc = 0, pin_status = 0;  // descriptors and statuses in the pinned staging buffer
+    unsigned int max_tile_log2 = 0;
+    unsigned long long max_n = 0;
+};
+
+int grow_pinned(uint8_t **buf, size_t *cap, size_t need) {
+    if (need <= *cap) return kOK;
+    cudaFreeHost(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMallocHost((void **)buf, need) != cudaSuccess) { cudaGetLastError(); *buf = nullptr; return kErrNomem; }
+    *cap = need;
+    return kOK;
+}
+
+// Cut the live streams into groups and lay out their device copies, workspaces and pinned staging.
+// Consecutive streams whose host bytes follow each other share one copy: copies in bridge gaps of up to
+// kBatchHostGap bytes and keep 16-byte offsets (the device streams stay 16-byte aligned); copies out join
+// back-to-back outputs only, so no caller byte outside an output is written.
+void plan_host_groups(int n, const void *const *h_comps, const size_t *comp_lens, void *const *h_outs,
+                      const size_t *out_lens, const std::vector<aceapex_info> &info, const std::vector<char> &live,
+                      uint64_t target, std::vector<HostGroup> &groups, std::vector<uint64_t> &d_comp,
+                      std::vector<uint64_t> &d_out, uint64_t &c_end, uint64_t &o_end, uint64_t &ws_end,
+                      uint64_t &pin_end, uint64_t &wave_need, uint64_t &n_wave) {
+    c_end = o_end = ws_end = pin_end = wave_need = n_wave = 0;
+    for (int i = 0; i < n;) {
+        HostGroup G;
+        uint64_t acc = 0, in_d = 0, out_d = 0;
+        uint8_t *in_h = nullptr, *in_e = nullptr, *out_h = nullptr, *out_e = nullptr;
+        for (; i < n && acc < target; i++) {
+            if (!live[i]) continue;
+            const aceapex_info &I = info[i];
+            uint8_t *hc = (uint8_t *)h_comps[i], *ho = (uint8_t *)h_outs[i];
+            if (in_h && hc >= in_e && (uint64_t)(hc - in_e) <= kBatchHostGap && ((hc - in_h) & 15) == 0) {
+                in_e = std::max(in_e, hc + comp_lens[i]);
+            } else {
+                if (in_h) { G.in.push_back({in_d, in_h, (uint64_t)(in_e - in_h)}); c_end = in_d + (uint64_t)(in_e - in_h); }
+                in_d = align16(c_end);
+                in_h = hc;
+                in_e = hc + comp_lens[i];
+            }
+            d_comp[i] = in_d + (uint64_t)(hc - in_h);
+            if (out_h && ho == out_e) {
+                out_e += out_lens[i];
+            } else {
+                if (out_h) { G.out.push_back({out_d, out_h, (uint64_t)(out_e - out_h)}); o_end = out_d + (uint64_t)(out_e - out_h); }
+                out_d = align16(o_end) + ((uintptr_t)ho & 15);  // the device copy keeps the host's alignment
+                out_h = ho;
+                out_e = ho + out_lens[i];
+            }
+            d_out[i] = out_d + (uint64_t)(ho - out_h);
+            acc += I.decoded_len;
+            if (use_wave(I)) {
+                G.wave.push_back(i);
+                wave_need = std::max<uint64_t>(wave_need, layout_one(I, true).total);
+                n_wave++;
+            } else {
+                G.flat.push_back(i);
+                G.max_tile_log2 = std::max(G.max_tile_log2, I.tile_log2);
+                G.max_n = std::max<unsigned long long>(G.max_n, I.decoded_len);
+                G.lm_at.push_back(G.lm_words);
+                G.tiles += I.n_tiles;
+                G.lm_words += litmap_words(I.decoded_len);
+            }
+        }
+        if (in_h) { G.in.push_back({in_d, in_h, (uint64_t)(in_e - in_h)}); c_end = in_d + (uint64_t)(in_e - in_h); }
+        if (out_h) { G.out.push_back({out_d, out_h, (uint64_t)(out_e - out_h)}); o_end = out_d + (uint64_t)(out_e - out_h); }
+        if (G.flat.empty() && G.wave.empty()) continue;
+        const size_t nf = G.flat.size();
+        if (nf) {
+            G.L = layout(std::max<int>((int)nf, 2), G.tiles, false, nullptr, G.lm_words);  // descriptor table in memory
+            G.ws_at = ws_end;
+            ws_end = up(ws_end + G.L.total);
+            G.pin_desc = pin_end;
+            pin_end = up(pin_end + sizeof(StreamDesc) * nf);
+        }
+        G.pin_status = pin_end;
+        pin_end = up(pin_end + 4 * (nf + G.wave.size()));
+        groups.push_back(std::move(G));
+    }
+}
+}  // namespace
+
+int aceapex_decode_batch_host(int n, const void *const *h_comps, const size_t *comp_lens, void *const *h_outs,
+                              const size_t *out_lens, int32_t *statuses, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (n < 0 || (n > 0 && (!h_comps || !comp_lens || !h_outs || !out_lens || !statuses))) return kErrArg;
+    // headers straight from host memory: argument and header errors are known before any device work
+    std::vector<aceapex_info> info(n);
+    std::vector<char> live(n, 0);
+    uint64_t n_total = 0;
+    for (int i = 0; i < n; i++) {
+        statuses[i] = 0;
+        if (!h_comps[i] || comp_lens[i] < kStreamHeader || (!h_outs[i] && out_lens[i])) { statuses[i] = kErrArg; continue; }
+        aceapex_info &I = info[i];
+        int r = parse_header((const uint8_t *)h_comps[i], kStreamHeader, &I);
+        if (!r && (I.comp_len != comp_lens[i] || I.decoded_len != out_lens[i])) r = kErrSize;
+        if (!r && I.decoded_len == 0 && (I.n_blocks || I.n_match || I.n_seq || I.max_depth)) r = kErrFormat;
+        if (r) { statuses[i] = r; continue; }
+        if (I.decoded_len == 0) continue;
+        live[i] = 1;
+        n_total += I.decoded_len;
+    }
+    auto first_error = [&]() {
+        for (int i = 0; i < n; i++) if (statuses[i]) return (int)statuses[i];
+        return (int)kOK;
+    };
+    if (n_total == 0) return first_error();
+    std::lock_guard<std::mutex> g(ctx().mu);
+    DevPool *p = nullptr;
+    int rc = pool_for_device(&p);
+    if (!rc) rc = host_path_init(*p);
+    if (rc) return rc;
+    std::vector<HostGroup> groups;
+    std::vector<uint64_t> d_comp(n, 0), d_out(n, 0);
+    uint64_t c_end, o_end, ws_end, pin_end, wave_need, n_wave;
+    plan_host_groups(n, h_comps, comp_lens, h_outs, out_lens, info, live,
+                     std::max<uint64_t>(n_total / kBatchHostGroups, 16ull << 20), groups, d_comp, d_out, c_end, o_end,
+                     ws_end, pin_end, wave_need, n_wave);
+    const uint64_t wave_at = ws_end, wst_at = up(wave_at + wave_need);
+    ws_end = up(wst_at + 4 * (n_wave + 1));
+    // every buffer is in place before the first copy: growing one frees the old one, which synchronises
+    rc = grow(&p->hb_comp, &p->hb_comp_cap, c_end + 16);
+    if (!rc) rc = grow(&p->hb_out, &p->hb_out_cap, o_end + 16);
+    if (!rc) rc = grow(&p->hb_ws, &p->hb_ws_cap, ws_end);
+    if (!rc) rc = grow_pinned(&p->hb_pin, &p->hb_pin_cap, pin_end + 16);
+    if (rc) return rc;
+    uint8_t *ws = p->hb_ws;
+    for (HostGroup &G : groups) {
+        StreamDesc *D = (StreamDesc *)(p->hb_pin + G.pin_desc);
+        uint64_t tb = 0;
+        for (size_t k = 0; k < G.flat.size(); k++) {
+            const int i = G.flat[k];
+            D[k] = make_desc(p->hb_comp + d_comp[i], p->hb_out + d_out[i], info[i], tb);
+            D[k].litmap = (uint32_t *)(ws + G.ws_at + G.L.litmap) + G.lm_at[k];
+            tb += info[i].n_tiles;
+        }
+    }
+    // on a failure after work was enqueued, the call returns only once no copy touches the caller's buffers
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(p->s_in);
+        cudaStreamSynchronize(stream);
+        cudaStreamSynchronize(p->s_out);
+        return code;
+    };
+    // ordered after the caller's earlier work on `stream`; the groups' control regions (head, states,
+    // statuses, descriptors, tile flags: flags hold launch epochs) start zeroed, the wavefront workspace too
+    if (cudaEventRecord(p->ev_dec[0], stream) != cudaSuccess || cudaStreamWaitEvent(p->s_in, p->ev_dec[0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(p->s_out, p->ev_dec[0], 0) != cudaSuccess)
+        return fail(cuda_fail(cudaErrorUnknown));
+    for (const HostGroup &G : groups) {
+        if (G.flat.empty()) continue;
+        if (cudaMemsetAsync(ws + G.ws_at, 0, G.L.litmap, stream) != cudaSuccess ||
+            cudaMemcpyAsync(ws + G.ws_at + G.L.descs, p->hb_pin + G.pin_desc, sizeof(StreamDesc) * G.flat.size(),
+                            cudaMemcpyHostToDevice, stream) != cudaSuccess)
+            return fail(cuda_fail(cudaErrorUnknown));
+    }
+    if (n_wave && cudaMemsetAsync(ws + wave_at, 0, wave_need, stream) != cudaSuccess) return fail(cuda_fail(cudaErrorUnknown));
+    LaunchCfg cfg = ctx().cfg;
+    cfg.num_sms = p->num_sms;
+    int32_t *wave_status = (int32_t *)(ws + wst_at);
+    uint64_t wk = 0;
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+        const HostGroup &G = groups[gi];
+        const int e = (int)(gi % kHostSlices);  // an event is re-recorded only after its waits were enqueued
+        for (const HostRun &r : G.in)
+            if (cudaMemcpyAsync(p->hb_comp + r.dev, r.host, r.len, cudaMemcpyHostToDevice, p->s_in) != cudaSuccess)
+                return fail(cuda_fail(cudaErrorUnknown));
+        if (cudaEventRecord(p->ev_in[e], p->s_in) != cudaSuccess || cudaStreamWaitEvent(stream, p->ev_in[e], 0) != cudaSuccess)
+            return fail(cuda_fail(cudaErrorUnknown));
+        const size_t nf = G.flat.size();
+        uint8_t *gws = ws + G.ws_at;
+        if (nf) {
+            LaunchArgs a{};
+            a.n_streams = (int)nf;
+            a.total_tiles = G.tiles;
+            a.wait_ns = ctx().wait_ns;
+            a.withhold = ctx().withhold;
+            a.max_tile_log2 = G.max_tile_log2;
+            a.max_n = G.max_n;
+            if (nf == 1) a.one = *(const StreamDesc *)(p->hb_pin + G.pin_desc);
+            cudaError_t ce = launch_flat(cfg, (WsHead *)(gws + G.L.head), (StreamState *)(gws + G.L.sst),
+                                         (uint32_t *)(gws + G.L.flags), nf > 1 ? (const StreamDesc *)(gws + G.L.descs) : nullptr,
+                                         a, (int32_t *)(gws + G.L.status), stream);
+            if (ce != cudaSuccess) return fail(cuda_fail(ce));
+        }
+        const uint64_t wk0 = wk;
+        for (int i : G.wave) {
+            rc = enqueue_one(p->hb_comp + d_comp[i], p->hb_out + d_out[i], info[i], ws + wave_at, layout_one(info[i], true),
+                             wave_status + wk, p->num_sms, stream);
+            if (rc) return fail(rc);
+            wk++;
+        }
+        if (cudaEventRecord(p->ev_dec[e], stream) != cudaSuccess || cudaStreamWaitEvent(p->s_out, p->ev_dec[e], 0) != cudaSuccess)
+            return fail(cuda_fail(cudaErrorUnknown));
+        for (const HostRun &r : G.out)
+            if (cudaMemcpyAsync(r.host, p->hb_out + r.dev, r.len, cudaMemcpyDeviceToHost, p->s_out) != cudaSuccess)
+                return fail(cuda_fail(cudaErrorUnknown));
+        if ((nf && cudaMemcpyAsync(p->hb_pin + G.pin_status, gws + G.L.status, 4 * nf, cudaMemcpyDeviceToHost, p->s_out) !=
+                       cudaSuccess) ||
+            (!G.wave.empty() && cudaMemcpyAsync(p->hb_pin + G.pin_status + 4 * nf, wave_status + wk0, 4 * G.wave.size(),
+                                                cudaMemcpyDeviceToHost, p->s_out) != cudaSuccess))
+            return fail(cuda_fail(cudaErrorUnknown));
+    }
+    cudaError_t ce = cudaStreamSynchronize(p->s_out);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->s_in);
+    if (ce != cudaSuccess) return fail(cuda_fail(ce));
+    for (const HostGroup &G : groups) {
+        const int32_t *st = (const int32_t *)(p->hb_pin + G.pin_status);
+        for (size_t k = 0; k < G.flat.size(); k++) statuses[G.flat[k]] = st[k];
+        for (size_t k = 0; k < G.wave.size(); k++) statuses[G.wave[k]] = st[G.flat.size() + k];
+    }
+    return first_error();
 }
 
 int aceapex_choose_device(const aceapex_info *info, const aceapex_device_model *model, double *cpu_s, double *gpu_s) {
