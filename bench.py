@@ -84,9 +84,9 @@ def stream_stats(comp: np.ndarray):
 # of the same workload (`dram__bytes_read.sum + dram__bytes_write.sum` of one launch / decoded bytes),
 # scaled to the bench's size by the decoded bytes.  An entry is removed when its kernel changes.
 MEASURED_TRAFFIC_PER_BYTE = {
-    ("fastq-flat", "k_flat"): 2.6845,  # 439,158,016 + 281,489,152 bytes, 256 MiB flattened FASTQ, one k_flat launch
+    ("fastq-flat", "k_flat"): 2.6900,  # 439,667,456 + 282,425,344 bytes, 256 MiB flattened FASTQ, one k_flat launch
     ("text", "k_flow"): 7.1578,        # 1,504,972,800 + 416,439,552 bytes, 256 MiB deep text, one k_flow launch
-    ("batch", "k_flat"): 1.9065,       # 890,452,053 + 1,158,055,339 bytes, 512 streams of the batch (1,074,488,070
+    ("batch", "k_flat"): 1.9070,       # 890,503,936 + 1,158,538,752 bytes, 512 streams of the batch (1,074,488,070
                                        # decoded bytes), per k_flat launch (mean of 3)
 }
 

@@ -80,3 +80,25 @@ def test_encoder_rejects_bad_params(lib):
         ax.encode(b"abc", long_bits=16, long_chain=17)
     with pytest.raises(oracle.OracleError):
         oracle.encode(b"abc", long_bits=16, long_chain=0)
+
+
+def test_batch_host_argument_and_header_errors_without_a_gpu(lib):
+    """aceapex_decode_batch_host settles argument, size and header errors from host memory, before any device
+    work: a batch with no stream left to decode returns without touching the GPU."""
+    assert lib.aceapex_decode_batch_host(-1, None, None, None, None, None, None) == ax.ERR_ARG
+    assert lib.aceapex_decode_batch_host(1, None, None, None, None, None, None) == ax.ERR_ARG
+    assert lib.aceapex_decode_batch_host(0, None, None, None, None, None, None) == 0
+    x = synth.make("text", 5000, 3)
+    good = oracle.encode(x, block_log2=12, tile_log2=8, flatten=2)
+    bad_magic = good.copy()
+    bad_magic[0] ^= 0xFF
+    rc_o, _ = oracle.decode_rc(bad_magic, out_len=x.size)
+    empty = oracle.encode(np.zeros(0, np.uint8))
+    comps = [good[:40].copy(), good, bad_magic, empty]
+    outs = [np.empty(x.size, np.uint8), np.empty(x.size + 3, np.uint8), np.empty(x.size, np.uint8),
+            np.zeros(0, np.uint8)]
+    st = ax.decode_batch_host(comps, outs, stream=0)  # stream 0: no torch CUDA call
+    assert list(st) == [ax.ERR_ARG, ax.ERR_SIZE, rc_o, 0]
+    b = ax.HostBatch(comps, outs)
+    assert ax.decode_batch_host_status(b, 0) == ax.ERR_ARG  # the first failing status in stream order
+    assert ax.decode_batch_host([empty], [np.zeros(0, np.uint8)], stream=0).tolist() == [0]
