@@ -72,21 +72,47 @@ def build_cpupar(force: bool = False) -> str:
     return _PAR_PATH
 
 
-def cpupar_decode_rc(comp, out_len: int | None = None, threads: int | None = None):
-    """Block-parallel CPU decode (§3.1: threads over blocks in order): (status, bytes or None)."""
+def _par_lib():
     global _par
     with _lock:
         if _par is None:
             lib = ctypes.CDLL(build_cpupar())
             lib.cpupar_decode.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]
             lib.cpupar_decode.restype = ctypes.c_int
+            lib.cpupar_decode_batch.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            lib.cpupar_decode_batch.restype = ctypes.c_int
             _par = lib
+    return _par
+
+
+def cpupar_decode_rc(comp, out_len: int | None = None, threads: int | None = None):
+    """Block-parallel CPU decode (§3.1: threads over blocks in order): (status, bytes or None)."""
     c = _u8(comp)
     if out_len is None:
         out_len = int.from_bytes(bytes(c[16:24]), "little")
     out = np.zeros(max(out_len, 1), dtype=np.uint8)
-    rc = _par.cpupar_decode(c.ctypes.data, c.size, out.ctypes.data, out_len, int(threads or os.cpu_count() or 1))
+    rc = _par_lib().cpupar_decode(c.ctypes.data, c.size, out.ctypes.data, out_len, int(threads or os.cpu_count() or 1))
     return rc, (out[:out_len] if rc == 0 else None)
+
+
+def cpupar_decode_batch_rc(comps, out_lens=None, threads: int | None = None, outs=None):
+    """Block-parallel CPU decode of n independent streams from one queue of (stream, block) units (§3.1
+    per stream, §7.5 across streams): (first failing status or 0, per-stream statuses, outputs).  `outs`:
+    optional preallocated uint8 arrays (one per stream) to decode into."""
+    cs = [_u8(c) for c in comps]
+    n = len(cs)
+    if out_lens is None:
+        out_lens = [int.from_bytes(bytes(c[16:24]), "little") if c.size >= 24 else 0 for c in cs]
+    if outs is None:
+        outs = [np.zeros(max(int(m), 1), dtype=np.uint8) for m in out_lens]
+    cp = (ctypes.c_void_p * max(n, 1))(*[c.ctypes.data for c in cs])
+    cl = (ctypes.c_uint64 * max(n, 1))(*[c.size for c in cs])
+    op = (ctypes.c_void_p * max(n, 1))(*[o.ctypes.data for o in outs])
+    ol = (ctypes.c_uint64 * max(n, 1))(*[int(m) for m in out_lens])
+    st = np.zeros(max(n, 1), np.int32)
+    rc = _par_lib().cpupar_decode_batch(n, cp, cl, op, ol, st.ctypes.data, int(threads or os.cpu_count() or 1))
+    return rc, st[:n], [o[:int(m)] for o, m in zip(outs, out_lens)]
 
 
 def _load():

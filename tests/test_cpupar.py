@@ -49,7 +49,11 @@ def test_rejects_wrong_size_and_bad_stream():
     bad = comp.copy()
     bad[0] ^= 1
     assert oracle.cpupar_decode_rc(bad, out_len=x.size, threads=2)[0] == -2
-    # a match whose source does not precede it
+    assert oracle.cpupar_decode_rc(_bad_source_stream(comp), threads=2)[0] == -4
+
+
+def _bad_source_stream(comp):
+    """The stream with block 0's first match given a source that does not precede it."""
     r, L, s, _ = oracle.parse(comp)
     b0 = int.from_bytes(bytes(comp[64:72]), "little")
     w = int(comp[b0 + 20])
@@ -58,6 +62,71 @@ def test_rejects_wrong_size_and_bad_stream():
     len_bytes = int.from_bytes(bytes(comp[b0 + 16:b0 + 20]), "little")
     a16 = lambda v: (v + 15) & ~15
     o_off = b0 + a16(a16(a16(32 + 20 * n_tiles) + cmd_bytes) + len_bytes)
-    bad2 = comp.copy()
-    bad2[o_off:o_off + w] = np.frombuffer(min(int(r[0]) + 1, (1 << (8 * w)) - 1).to_bytes(w, "little"), np.uint8)
-    assert oracle.cpupar_decode_rc(bad2, threads=2)[0] == -4
+    bad = comp.copy()
+    bad[o_off:o_off + w] = np.frombuffer(min(int(r[0]) + 1, (1 << (8 * w)) - 1).to_bytes(w, "little"), np.uint8)
+    return bad
+
+
+def _batch_pool(seed):
+    """Streams of every generator and several encoder modes, many of one or two blocks, some of many, plus
+    empty and one-byte streams: (inputs, streams)."""
+    rng = np.random.default_rng(seed)
+    xs, cs = [], []
+    for i in range(40):
+        kind = KINDS[i % len(KINDS)]
+        mode = MODES[(i // len(KINDS)) % len(MODES)]
+        n = int(rng.choice([0, 1, 3000, 60_000, 200_000, 900_000]))
+        x = synth.make(kind, n, 100 + i)
+        xs.append(x)
+        cs.append(oracle.encode(x, block_log2=16, tile_log2=12, **mode))
+    return xs, cs
+
+
+@pytest.mark.parametrize("threads", [1, 4, 16, 64])
+def test_batch_decode_equals_oracle(threads):
+    xs, cs = _batch_pool(7)
+    rc, st, outs = oracle.cpupar_decode_batch_rc(cs, [x.size for x in xs], threads=threads)
+    assert rc == 0 and (st == 0).all(), st
+    for c, x, o in zip(cs, xs, outs):
+        assert np.array_equal(o, oracle.decode(c)) and np.array_equal(o, x)
+
+
+def test_batch_of_deep_cross_block_streams():
+    """Unflattened text with tiny blocks: waits inside each stream while other streams' blocks run."""
+    xs = [synth.make("text", 400_000, 30 + k) for k in range(6)]
+    cs = [oracle.encode(x, block_log2=10, tile_log2=6) for x in xs]
+    rc, st, outs = oracle.cpupar_decode_batch_rc(cs, [x.size for x in xs], threads=16)
+    assert rc == 0 and (st == 0).all()
+    for x, o in zip(xs, outs):
+        assert np.array_equal(o, x)
+
+
+def test_batch_errors_per_stream_and_first_error_returned():
+    x = synth.make("text", 50_000, 1)
+    good = oracle.encode(x, block_log2=12)
+    bad_magic = good.copy()
+    bad_magic[0] ^= 1
+    cs = [good, bad_magic, good, good]
+    lens = [x.size, x.size, x.size + 1, x.size]
+    rc, st, outs = oracle.cpupar_decode_batch_rc(cs, lens, threads=8)
+    # the same statuses as one-at-a-time decodes, the good streams still decoded
+    assert list(st) == [oracle.cpupar_decode_rc(c, m, threads=2)[0] for c, m in zip(cs, lens)] == [0, -2, -3, 0]
+    assert rc == -2
+    assert np.array_equal(outs[0], x) and np.array_equal(outs[3], x)
+
+
+def test_batch_stream_failing_in_its_first_block_does_not_stall_the_others():
+    """Block 0 of the middle stream fails; its later blocks, which wait on block 0, are released and
+    skipped, and the streams around it decode."""
+    x = synth.make("text", 50_000, 1)
+    good = oracle.encode(x, block_log2=12)
+    cs = [good, _bad_source_stream(good), good]
+    for threads in (2, 8):
+        rc, st, outs = oracle.cpupar_decode_batch_rc(cs, [x.size] * 3, threads=threads)
+        assert rc == -4 and list(st) == [0, -4, 0]
+        assert np.array_equal(outs[0], x) and np.array_equal(outs[2], x)
+
+
+def test_empty_batch():
+    rc, st, outs = oracle.cpupar_decode_batch_rc([], [], threads=4)
+    assert rc == 0 and st.size == 0 and outs == []
