@@ -161,7 +161,8 @@ int aceapex_decode_batch(int n, const void *const *comps, const size_t *comp_len
  * streams (read only), copies out join only outputs that are back to back, so no byte outside the outputs
  * is written.  Host buffers are only read / written during the call; work is ordered after the caller's
  * earlier work on `stream`.  Returns 0 when every stream decoded, else the first failing status in stream
- * order; ACEAPEX_ERR_NOMEM when the device or pinned buffers cannot be allocated.
+ * order; ACEAPEX_ERR_ARG when n < 0 or an array is null (statuses untouched); ACEAPEX_ERR_NOMEM when the
+ * device or pinned buffers cannot be allocated.  The call holds the context's lock until it returns.
  */
 int aceapex_decode_batch_host(int n, const void *const *h_comps, const size_t *comp_lens, void *const *h_outs,
                               const size_t *out_lens, int32_t *statuses, void *stream);
