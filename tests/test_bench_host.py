@@ -90,3 +90,15 @@ def test_serve_mix_and_schedule():
     assert abs(gaps.mean() - 1e-3) < 1e-4                            # rate 1000 per second
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1                 # exponential gaps
     assert w1.min() >= 0 and w1.max() < 32
+
+
+def test_parallel_cpu_baseline_legs():
+    """The bench's block-parallel CPU figures: one queue over a batch of streams, and streams one at a time;
+    both decode the streams exactly (the batch leg checks its first pass against the inputs)."""
+    xs = [synth.make(k, n, 60 + i) for i, (k, n) in enumerate([("text", 300_000), ("fastq", 200_000),
+                                                               ("random", 5_000), ("rle7", 0)])]
+    cs = [oracle.encode(x, block_log2=16, tile_log2=12, flatten=2, min_emit=6) for x in xs]
+    for batch in (True, False):
+        line = bench._cpu_par_line(cs, xs, 0.2, "test streams", batch=batch)
+        assert line["value"] > 0 and line["cores"] >= 1 and line["unit"] == "GB/s"
+        assert ("queue" in line["kind"]) == batch
